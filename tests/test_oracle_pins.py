@@ -1,0 +1,564 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check uses a closed form,
+a value printed in the paper, an invariant, a second independent formulation
+(tests/lattice_np.py) or brute force.
+"""
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests import lattice_np as L
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_su3(n, seed):
+    return synth.haar_su3(n, seed)
+
+
+# --------------------------------------------------------------------------
+# Counter-based generator: published SplitMix64 outputs
+# --------------------------------------------------------------------------
+
+def test_splitmix64_published_vectors():
+    with open(os.path.join(GOLDEN, "splitmix64_seed1234567.json")) as f:
+        g = json.load(f)
+    got = [O.splitmix64(g["seed"], i) for i in range(len(g["values"]))]
+    assert got == g["values"]
+    # the shared input generator implements the same published stream
+    assert [int(v) for v in synth.splitmix64(g["seed"], np.arange(5))] == g["values"]
+
+
+# --------------------------------------------------------------------------
+# Z(3) label, Eq. (centre_element)
+# --------------------------------------------------------------------------
+
+def test_label_of_centre_elements():
+    for n in (-1, 0, 1):
+        Z = np.exp(2j * np.pi * n / 3) * np.eye(3)
+        assert O.label_matrix(Z) == n
+
+
+def test_label_sector_interiors_and_ties():
+    def diag_tr(t):
+        # a matrix whose trace is t (labels depend on the trace only)
+        return np.diag([t, 0, 0])
+    cases = {
+        0.0: 0, 0.9: 0, -0.9: 0,                  # arg in (-pi/3, pi/3)
+        1.2: 1, 2.0: 1, 3.0: 1,                   # arg in (pi/3, pi)
+        -1.2: -1, -2.0: -1, -3.0: -1,             # arg in (-pi, -pi/3)
+    }
+    for arg, n in cases.items():
+        assert O.label_matrix(diag_tr(2.0 * np.exp(1j * arg))) == n, arg
+    # common end points (the reading stated in the oracle)
+    assert O.label_matrix(diag_tr(-1.0 + 0j)) == 1        # arg = pi
+    assert O.label_matrix(diag_tr(-1.0 - 0j)) == 1        # -0 imaginary part taken as +0
+    assert O.label_matrix(diag_tr(0j)) == 0               # Tr U = 0
+
+
+def test_label_matches_nearest_centre_on_haar_matrices():
+    U = _rand_su3(20000, seed=11)
+    lab = O.labels((1, 1, 1, 5000), U.reshape(4, 5000, 3, 3)).reshape(-1)
+    ref = L.label_nearest_centre(np.trace(U, axis1=1, axis2=2))
+    assert np.array_equal(lab, ref)
+    # Haar measure is Z(3)-invariant: each sector holds ~1/3 of the matrices
+    frac = [np.mean(lab == n) for n in (-1, 0, 1)]
+    assert all(abs(f - 1 / 3) < 0.02 for f in frac)
+
+
+# --------------------------------------------------------------------------
+# Staples and the stout generator, Eqs. (plaq_staples), (generator), (over-improvement)
+# --------------------------------------------------------------------------
+
+def test_overimproved_coefficients_and_alpha_min():
+    # eps = 1 is standard smearing (Sec. III): rectangles drop out.
+    assert O.overimproved_coeffs(1.0, 1.0) == (1.0, 0.0)
+    # alpha_min from the extremal staples (S = -3, R = 18, Appendix B):
+    # Re L1 = (1 - a) + a/6 (c0 S + c1 R) < 0.  The paper prints 0.4486 at eps = -0.25.
+    c0, c1 = O.overimproved_coeffs(-0.25, 1.0)
+    amin = 1.0 / (1.0 - (c0 * -3.0 + c1 * 18.0) / 6.0)
+    assert abs(amin - 0.4486) < 5e-5
+    # and the paper's closed form, Eq. (alpha_condition_ape), for other eps, u0
+    for eps, u0 in [(-2.5, 1.0), (-1.0, 0.9), (0.0, 0.85), (0.5, 1.0)]:
+        c0, c1 = O.overimproved_coeffs(eps, u0)
+        amin = 1.0 / (1.0 - (c0 * -3.0 + c1 * 18.0) / 6.0)
+        closed = -6.0 / (2 * eps - 11 + 1.5 * (eps - 1) / u0 ** 2)
+        assert abs(amin - closed) < 1e-13
+
+
+def test_staples_of_pure_z3_field_are_proportional_to_identity():
+    dims = (4, 4, 4, 4)
+    lab = synth.iid_labels(dims, seed=5, p0=0.4, p_plus=0.3)
+    U = O.links_from_labels(dims, lab)
+    for mu, x in [(0, (0, 0, 0, 0)), (2, (1, 3, 2, 0)), (3, (3, 1, 0, 2))]:
+        for eps in (1.0, -0.25):
+            c0, c1 = O.overimproved_coeffs(eps)
+            S = O.staple_sum(dims, U, mu, x, c0, c1)
+            assert np.allclose(S - S[0, 0] * np.eye(3), 0, atol=1e-13)
+            Q = O.stout_generator(S @ L.dag(U[mu, np.ravel_multi_index(x[::-1], dims[::-1])]))
+            assert np.abs(Q).max() < 1e-13
+
+
+def test_staple_sum_example_two_identity_four_centre():
+    # Sec. III.A: 2 I + 4 exp(+-2 pi i/3) = +-i 2 sqrt(3) I  (~ +-3.464 i)
+    dims = (4, 4, 4, 4)
+    for n in (1, -1):
+        lab = np.zeros((4, 256), dtype=np.int8)
+        x = np.array([1, 1, 1, 1])
+        mu = 0
+
+        def site(y):
+            y = np.mod(y, 4)
+            return y[0] + 4 * (y[1] + 4 * (y[2] + 4 * y[3]))
+        for nu in (1, 2):
+            e = np.eye(4, dtype=int)[nu]
+            lab[mu, site(x + e)] = n      # U_mu(x+nu) in the upper staple
+            lab[mu, site(x - e)] = n      # U_mu(x-nu) in the lower staple
+        U = O.links_from_labels(dims, lab)
+        S = O.staple_sum(dims, U, mu, tuple(x), 1.0, 0.0)
+        assert np.allclose(S, 1j * n * 2 * np.sqrt(3) * np.eye(3), atol=1e-13)
+        assert abs(S[0, 0].imag - n * 3.464) < 1e-3
+
+
+def test_staple_gauge_covariance():
+    # Sigma -> G(x) Sigma G^dag(x+mu), Sec. II.A
+    dims = (4, 4, 4, 4)
+    V = 256
+    U = synth.haar_field(dims, seed=21)
+    G = synth.random_gauge(dims, seed=22)
+    UG = O.gauge_transform(dims, U, G)
+    for eps in (1.0, -0.25):
+        c0, c1 = O.overimproved_coeffs(eps)
+        for mu, x in [(0, (0, 1, 2, 3)), (3, (3, 3, 0, 1))]:
+            s = x[0] + 4 * (x[1] + 4 * (x[2] + 4 * x[3]))
+            xp = list(x)
+            xp[mu] = (xp[mu] + 1) % 4
+            sp = xp[0] + 4 * (xp[1] + 4 * (xp[2] + 4 * xp[3]))
+            S = O.staple_sum(dims, U, mu, x, c0, c1)
+            SG = O.staple_sum(dims, UG, mu, x, c0, c1)
+            assert np.allclose(SG, G[s] @ S @ L.dag(G[sp]), atol=1e-12)
+    assert V == 256
+
+
+def _fd_action(Ulat, c0, c1):
+    """W = 2 c0 sum_{x, mu<nu} Re Tr P + 2 c1 sum_{x, mu != nu} Re Tr R(2x1)."""
+    W = 0.0
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            if mu < nu:
+                W += 2 * c0 * np.real(L.tr(L.plaquette(Ulat, mu, nu))).sum()
+            if c1 != 0.0:
+                W += 2 * c1 * np.real(L.tr(L.rectangle(Ulat, mu, nu))).sum()
+    return W
+
+
+@pytest.mark.parametrize("eps", [1.0, -0.25])
+def test_generator_is_action_gradient_finite_difference(eps):
+    """Q_mu(x) = T^a d^a W (Sec. II.B) checked by central differences on a
+    random SU(3) field; this pins every staple and rectangle path and the
+    normalisation of Eq. (generator)."""
+    dims = (4, 4, 4, 4)
+    U = synth.haar_field(dims, seed=31)
+    c0, c1 = O.overimproved_coeffs(eps)
+    T = L.gell_mann_generators()
+    h = 1e-4
+    for mu, x in [(1, (2, 0, 3, 1)), (3, (0, 2, 1, 3))]:
+        s = x[0] + 4 * (x[1] + 4 * (x[2] + 4 * x[3]))
+        S = O.staple_sum(dims, U, mu, x, c0, c1)
+        Q = O.stout_generator(S @ L.dag(U[mu, s]))
+        Qfd = np.zeros((3, 3), dtype=np.complex128)
+        for a in range(8):
+            vals = []
+            for sg in (+1, -1):
+                Up = U.copy()
+                Up[mu, s] = O.expm(sg * h * T[a]) @ U[mu, s]
+                vals.append(_fd_action(L.to_lat(Up, dims), c0, c1))
+            Qfd += T[a] * (vals[0] - vals[1]) / (2 * h)
+        assert np.abs(Q - Qfd).max() < 2e-6, np.abs(Q - Qfd).max()
+        assert np.abs(Q + L.dag(Q)).max() < 1e-13            # anti-Hermitian
+        assert abs(np.trace(Q)) < 1e-13                       # traceless
+
+
+# --------------------------------------------------------------------------
+# Exponential
+# --------------------------------------------------------------------------
+
+def _random_traceless_hermitian(rng, n, scale):
+    A = rng.normal(size=(n, 3, 3)) + 1j * rng.normal(size=(n, 3, 3))
+    H = 0.5 * (A + L.dag(A))
+    H -= np.trace(H, axis1=1, axis2=2)[:, None, None] / 3 * np.eye(3)
+    nrm = np.linalg.norm(H, ord=2, axis=(1, 2))
+    return H * (scale / nrm)[:, None, None]
+
+
+def test_expm_against_eigendecomposition_and_closed_forms():
+    rng = np.random.default_rng(41)
+    for scale in (1e-6, 0.05, 0.5, 1.0, 2.0):
+        for H in _random_traceless_hermitian(rng, 30, scale):
+            X = 1j * H
+            E = O.expm(X)
+            assert np.abs(E - L.expm_eigh(X)).max() < 1e-13
+            assert np.abs(E @ L.dag(E) - np.eye(3)).max() < 1e-14
+            assert abs(np.linalg.det(E) - 1) < 1e-14
+    # near-degenerate spectra: two eigenvalues equal (and nearly equal)
+    for gap in (0.0, 1e-9, 1e-4):
+        lam = np.array([0.3, 0.3 + gap, -0.6 - gap])
+        Wm = _rand_su3(1, 42)[0]
+        H = Wm @ np.diag(lam) @ L.dag(Wm)
+        E = O.expm(1j * H)
+        assert np.abs(E - Wm @ np.diag(np.exp(1j * lam)) @ L.dag(Wm)).max() < 1e-13
+    # exp(0) = I exactly
+    assert np.array_equal(O.expm(np.zeros((3, 3))), np.eye(3))
+
+
+def test_expm_is_limit_of_euler_steps():
+    # lim (I + eps Q)^n = exp(eps Q) with eps = 1/n  (Sec. II.B)
+    rng = np.random.default_rng(43)
+    X = 1j * _random_traceless_hermitian(rng, 1, 0.7)[0]
+    n = 1 << 22
+    M = np.eye(3) + X / n
+    for _ in range(22):
+        M = M @ M
+    assert np.abs(M - O.expm(X)).max() < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Centrifuge preconditioning, Sec. IV
+# --------------------------------------------------------------------------
+
+def test_centrifuge_closed_forms():
+    dims = (4, 4, 4, 8)
+    V = 512
+    lab = synth.iid_labels(dims, seed=7, p0=0.5, p_plus=0.25)
+    omega = 0.02
+    U, sigma = O.centrifuge(dims, lab, omega, seed=1234, with_sigma=True)
+    m = sigma * 18 / (2 * np.pi)
+    assert np.allclose(m, np.round(m), atol=1e-12)            # sigma = m 2pi/18
+    assert np.abs(m).max() <= 18
+    n = lab.astype(float)
+    d = np.diagonal(U, axis1=2, axis2=3)
+    # diagonal, off-diagonals exactly zero
+    off = U.copy()
+    for k in range(3):
+        off[..., k, k] = 0
+    assert not np.any(off)
+    ph = np.angle(d)
+    # sum of the three phases is 2 pi n (mod 2 pi): det Z' = 1
+    assert np.allclose(np.prod(d, axis=-1), 1.0, atol=1e-14)
+    # Tr Z' = (2 cos Lambda^- + 1) exp(2 pi i n / 3), Lambda^- = w (sigma - lambda)
+    lamminus = omega * (sigma - 2 * np.pi * n / 3)
+    tr_ref = (2 * np.cos(lamminus) + 1) * np.exp(2j * np.pi * n / 3)
+    assert np.allclose(d.sum(-1), tr_ref, atol=1e-14)
+    # two phases moved by +-w(sigma - lambda), the third unchanged
+    dev = np.angle(d * np.exp(-2j * np.pi * n / 3)[..., None])
+    srt = np.sort(dev, axis=-1)
+    assert np.allclose(srt[..., 1], 0, atol=1e-14)
+    assert np.allclose(np.abs(srt[..., 0]), np.abs(lamminus), atol=1e-14)
+    # labels are preserved (omega < 1/4, condition w|m - 6n| < 6)
+    assert np.array_equal(O.labels(dims, U), lab)
+    assert np.all(omega * np.abs(m - 6 * n) < 6)
+    del ph, V
+
+
+def test_centrifuge_trivial_field_and_pair_distribution():
+    dims = (4, 4, 4, 4)
+    lab = np.zeros((4, 256), dtype=np.int8)
+    U = O.centrifuge(dims, lab, 0.1, seed=3)
+    assert np.array_equal(U, np.broadcast_to(np.eye(3), U.shape))   # m = 0, delta = 0
+    pairs = [O.centrifuge_pair(1234, 10 ** 6, mu, s) for mu in range(4) for s in range(3000)]
+    frac = np.bincount(pairs, minlength=3) / len(pairs)
+    assert np.all(np.abs(frac - 1 / 3) < 0.02)
+
+
+def test_centrifuge_extreme_staple_phase_bound():
+    # The extremes m = +18, n = -1 make |m - 6n| = 24, so w|m - 6n| < 6 needs
+    # w < 1/4 (Sec. IV.A).  Build that link: n_0(x) = -1 and every staple phase
+    # summing to +3 (lambda_nu(x+mu) = lambda_nu(x-nu) = -1, all else +1).
+    dims = (4, 4, 4, 4)
+    lab = np.ones((4, 256), dtype=np.int8)
+
+    def site(y):
+        y = np.mod(y, 4)
+        return y[0] + 4 * (y[1] + 4 * (y[2] + 4 * y[3]))
+    x0 = np.zeros(4, dtype=int)
+    e = np.eye(4, dtype=int)
+    lab[0, site(x0)] = -1
+    for nu in (1, 2, 3):
+        lab[nu, site(x0 + e[0])] = -1
+        lab[nu, site(x0 - e[nu])] = -1
+    w = 0.2499
+    U, sigma = O.centrifuge(dims, lab, w, seed=1, with_sigma=True)
+    m = sigma[0, 0] * 18 / (2 * np.pi)
+    assert abs(m - 18) < 1e-12
+    lamminus = w * (sigma[0, 0] + 2 * np.pi / 3)
+    assert 0 < 2 * np.cos(lamminus) + 1 < 2e-3           # just inside the bound
+    assert O.labels(dims, U)[0, 0] == -1                  # label preserved
+    # at w = 1/4 the factor 2 cos(Lambda^-) + 1 reaches 0: the oracle refuses w >= 1/4
+    assert abs(2 * np.cos(0.25 * (sigma[0, 0] + 2 * np.pi / 3)) + 1) < 1e-12
+    with pytest.raises(ValueError):
+        O.centrifuge(dims, lab, 0.25, seed=1)
+
+
+# --------------------------------------------------------------------------
+# Smoothing sweeps
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eps,schedule", [(1.0, O.ANNEALED), (-0.25, O.ANNEALED),
+                                          (-0.25, O.SIMULTANEOUS)])
+def test_stout_leaves_pure_z3_field_unchanged(eps, schedule):
+    # Sec. II.A: Q = 0 on a vortex field, in any gauge.
+    dims = (4, 4, 4, 4)
+    lab = synth.iid_labels(dims, seed=1)
+    U = O.links_from_labels(dims, lab)
+    out, rej = O.smooth(dims, U, lab, 3, 0.1, eps=eps, schedule=schedule, vp=True)
+    # Q vanishes identically; in floating point only rounding of the exactly
+    # cancelling trace terms remains
+    assert np.abs(out - U).max() < 1e-15
+    assert not rej.any()
+    # and after a random gauge transformation
+    G = synth.random_gauge(dims, seed=2)
+    UG = O.gauge_transform(dims, U, G)
+    outG, _ = O.smooth(dims, UG, None, 2, 0.1, eps=eps, schedule=schedule, vp=False)
+    assert np.abs(outG - UG).max() < 1e-13
+
+
+def _diag_restatement(dims, phi, ref, n_sweeps, rho, eps, vp):
+    """Sec. V.C: on diagonal links the iteration acts on phases alone.
+    phi: float [4][t][z][y][x][3].  Whole colour classes update at once."""
+    c0, c1 = (5 - 2 * eps) / 3, (eps - 1) / 12
+    e = np.eye(4, dtype=int)
+
+    def path_phase(steps):
+        off = np.zeros(4, dtype=int)
+        tot = 0.0
+        for d, sg in steps:
+            if sg > 0:
+                tot = tot + np.roll(phi[d], tuple(-off[::-1]), axis=(0, 1, 2, 3))
+                off = off + e[d]
+            else:
+                off = off - e[d]
+                tot = tot - np.roll(phi[d], tuple(-off[::-1]), axis=(0, 1, 2, 3))
+        return tot
+
+    refl = ref.reshape((4,) + L.lat_shape(dims))
+    for _ in range(n_sweeps):
+        for mu in range(4):
+            for c in range(4):
+                Sig = 0.0
+                for nu in range(4):
+                    if nu == mu:
+                        continue
+                    for s in (1, -1):
+                        Sig = Sig + c0 * np.exp(1j * path_phase([(nu, s), (mu, 1), (nu, -s)]))
+                        if c1:
+                            for p in ([(nu, s), (nu, s), (mu, 1), (nu, -s), (nu, -s)],
+                                      [(nu, s), (mu, 1), (mu, 1), (nu, -s), (mu, -1)],
+                                      [(mu, -1), (nu, s), (mu, 1), (mu, 1), (nu, -s)]):
+                                Sig = Sig + c1 * np.exp(1j * path_phase(p))
+                Om = Sig * np.exp(-1j * phi[mu])
+                q = Om.imag - Om.imag.sum(-1, keepdims=True) / 3
+                new = phi[mu] + rho * q
+                mask = L.colour_mask(dims, mu, c)
+                if vp:
+                    lab = L.label_nearest_centre(np.exp(1j * new).sum(-1))
+                    mask = mask & (lab == refl[mu])
+                phi[mu] = np.where(mask[..., None], new, phi[mu])
+    return phi
+
+
+@pytest.mark.parametrize("eps,vp,dims", [(1.0, True, (4, 4, 4, 4)),
+                                         (-0.25, True, (4, 4, 8, 4)),
+                                         (-0.25, False, (8, 4, 4, 4))])
+def test_annealed_smoothing_matches_diagonal_restatement(eps, vp, dims):
+    V = int(np.prod(dims))
+    lab = synth.iid_labels(dims, seed=9)
+    U0 = O.centrifuge(dims, lab, 0.05, seed=77)
+    rho = 0.3
+    out, rej = O.smooth(dims, U0, lab, 4, rho, eps=eps, vp=vp, nthreads=1)
+    # stays in the diagonal subgroup (Sec. V.C)
+    off = out.copy()
+    for k in range(3):
+        off[..., k, k] = 0
+    assert np.abs(off).max() < 1e-15
+    phi = np.angle(np.diagonal(U0, axis1=2, axis2=3)).reshape((4,) + L.lat_shape(dims) + (3,))
+    phi = _diag_restatement(dims, phi.copy(), lab, 4, rho, eps, vp)
+    ref = np.exp(1j * phi).reshape(4, V, 3)
+    assert np.abs(np.diagonal(out, axis1=2, axis2=3) - ref).max() < 1e-12
+    if vp:
+        assert np.array_equal(O.labels(dims, out), lab)
+
+
+def test_threads_do_not_change_annealed_result():
+    dims = (8, 4, 4, 8)
+    U = synth.haar_field(dims, seed=12)
+    a, ra = O.smooth(dims, U, None, 2, 0.1, eps=-0.25, vp=False, nthreads=1)
+    b, rb = O.smooth(dims, U, None, 2, 0.1, eps=-0.25, vp=False, nthreads=4)
+    assert np.array_equal(a, b)
+
+
+def test_colour_classes_are_conflict_free():
+    """No link of class (mu, c) lies on the staple or rectangle paths of another
+    link of the same class (brute force over the paths of Eq. over-improvement)."""
+    for dims in [(4, 4, 4, 4), (8, 4, 12, 4)]:
+        e = np.eye(4, dtype=int)
+        for mu in range(4):
+            paths = []
+            for nu in range(4):
+                if nu == mu:
+                    continue
+                for s in (1, -1):
+                    paths += [[(nu, s), (mu, 1), (nu, -s)],
+                              [(nu, s), (nu, s), (mu, 1), (nu, -s), (nu, -s)],
+                              [(nu, s), (mu, 1), (mu, 1), (nu, -s), (mu, -1)],
+                              [(mu, -1), (nu, s), (mu, 1), (mu, 1), (nu, -s)]]
+            offsets = set()
+            for p in paths:
+                off = np.zeros(4, dtype=int)
+                for d, sg in p:
+                    if sg > 0:
+                        if d == mu:
+                            offsets.add(tuple(off))
+                        off = off + e[d]
+                    else:
+                        off = off - e[d]
+                        if d == mu:
+                            offsets.add(tuple(off))
+            offsets.discard((0, 0, 0, 0))
+            for x in itertools.product(*[range(Ld) for Ld in dims]):
+                cx = O.colour(dims, mu, x)
+                for off in offsets:
+                    y = tuple((np.array(x) + np.array(off)) % np.array(dims))
+                    if y != x:
+                        assert O.colour(dims, mu, y) != cx, (dims, mu, x, off)
+
+
+def test_smoothing_gauge_equivariance_and_unitarity():
+    dims = (4, 4, 4, 4)
+    U = synth.haar_field(dims, seed=51)
+    G = synth.random_gauge(dims, seed=52)
+    for sched in (O.ANNEALED, O.SIMULTANEOUS):
+        a, _ = O.smooth(dims, U, None, 2, 0.08, eps=-0.25, schedule=sched, vp=False)
+        b, _ = O.smooth(dims, O.gauge_transform(dims, U, G), None, 2, 0.08, eps=-0.25,
+                        schedule=sched, vp=False)
+        assert np.abs(O.gauge_transform(dims, a, G) - b).max() < 1e-12
+        assert np.abs(L.mm(a, L.dag(a)) - np.eye(3)).max() < 1e-13
+        assert np.abs(np.linalg.det(a) - 1).max() < 1e-13
+
+
+def test_simultaneous_schedule_uses_previous_field():
+    dims = (4, 4, 4, 4)
+    U = synth.haar_field(dims, seed=61)
+    out, _ = O.smooth(dims, U, None, 1, 0.1, eps=-0.25, schedule=O.SIMULTANEOUS, vp=False)
+    c0, c1 = O.overimproved_coeffs(-0.25)
+    for mu, s in [(0, 0), (2, 77), (3, 255)]:
+        x = np.unravel_index(s, (4, 4, 4, 4))[::-1]
+        S = O.staple_sum(dims, U, mu, x, c0, c1)
+        Q = O.stout_generator(S @ L.dag(U[mu, s]))
+        assert np.abs(out[mu, s] - L.expm_eigh(0.1 * Q) @ U[mu, s]).max() < 1e-13
+
+
+def test_vortex_preservation_keeps_original_labels():
+    dims = (4, 4, 4, 8)
+    lab = synth.iid_labels(dims, seed=13)
+    U0 = O.centrifuge(dims, lab, 0.02, seed=1234)
+    # large steps force candidates across sector boundaries
+    out, rej = O.smooth(dims, U0, lab, 5, 0.5, eps=-0.25, vp=True)
+    assert rej.sum() > 0
+    assert np.array_equal(O.labels(dims, out), lab)
+    chk = O.vortex_check(dims, out, lab)
+    assert chk["n_label_diff"] == 0 and chk["n_charge_diff"] == 0
+    outn, _ = O.smooth(dims, U0, lab, 5, 0.5, eps=-0.25, vp=False)
+    assert O.vortex_check(dims, outn, lab)["n_label_diff"] > 0
+
+
+# --------------------------------------------------------------------------
+# Action and vortex charges
+# --------------------------------------------------------------------------
+
+def test_action_closed_forms():
+    dims = (4, 4, 4, 4)
+    V = 256
+    I = np.broadcast_to(np.eye(3), (4, V, 3, 3)).astype(np.complex128)
+    assert O.action(dims, I) == 0.0
+    lab = synth.iid_labels(dims, seed=3)
+    U = O.links_from_labels(dims, lab)
+    ch = O.centre_charges(dims, lab)
+    # Re Tr P = 3 cos(2 pi p / 3): a pierced plaquette contributes 2*(3 + 3/2)/72
+    expected = (2 * 4.5 / 72) * np.count_nonzero(ch) / V
+    assert abs(O.action(dims, U) - expected) < 1e-14
+    # independent numpy restatement of the per-site density on a random field
+    H = synth.haar_field(dims, seed=4)
+    m, Sx = O.action(dims, H, per_site=True)
+    Ul = L.to_lat(H, dims)
+    ref = 0.0
+    for mu in range(4):
+        for nu in range(4):
+            if mu != nu:
+                ref = ref + np.real(3 - L.tr(L.plaquette(Ul, mu, nu)))
+    ref = (ref / 72).reshape(-1)
+    assert np.abs(Sx - ref).max() < 1e-13
+    # random links: <Re Tr P> ~ 0 so <S> ~ 12*3/72 = 0.5
+    assert abs(m - 0.5) < 0.05
+
+
+def test_action_gauge_invariance():
+    dims = (4, 4, 8, 4)
+    U = synth.haar_field(dims, seed=71)
+    G = synth.random_gauge(dims, seed=72)
+    assert abs(O.action(dims, U) - O.action(dims, O.gauge_transform(dims, U, G))) < 1e-13
+
+
+def test_centre_charges_from_z3_plaquette_products():
+    dims = (4, 4, 4, 4)
+    lab = synth.iid_labels(dims, seed=17, p0=0.34, p_plus=0.33)
+    U = L.to_lat(O.links_from_labels(dims, lab), dims)
+    ch = O.centre_charges(dims, lab)
+    k = 0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            p = L.label_nearest_centre(L.tr(L.plaquette(U, mu, nu))).reshape(-1)
+            assert np.array_equal(ch[k], p)
+            k += 1
+
+
+# --------------------------------------------------------------------------
+# MaxReTr cooling (input recipe)
+# --------------------------------------------------------------------------
+
+def test_cooling_lowers_action_and_stays_in_su3():
+    dims = (4, 4, 4, 4)
+    U = synth.haar_field(dims, seed=81)
+    s0 = O.action(dims, U)
+    c1 = O.cool(dims, U, 1)
+    c5 = O.cool(dims, U, 5)
+    assert O.action(dims, c1) < s0 and O.action(dims, c5) < O.action(dims, c1)
+    assert np.abs(L.mm(c5, L.dag(c5)) - np.eye(3)).max() < 1e-13
+    assert np.abs(np.linalg.det(c5) - 1).max() < 1e-13
+
+
+def test_cooling_leaves_vortex_field_with_positive_overlap_unchanged():
+    # Sec. III: where r cos(phi) > 0 every T^c is the identity.  A Z(3) pure-gauge
+    # field n_mu(x) = g(x) - g(x+mu) has every staple sum equal to 6 Z_mu(x),
+    # so phi = 0 on every link and one cooling sweep changes nothing.
+    dims = (4, 4, 4, 4)
+    V = 256
+    g = (synth.iid_labels(dims, seed=23, p0=0.34, p_plus=0.33)[0]).astype(int)
+    lab = np.zeros((4, V), dtype=np.int8)
+    for mu in range(4):
+        gl = g.reshape(L.lat_shape(dims))
+        d = gl - L.shift(gl, mu, 1)
+        lab[mu] = (((d + 1) % 3) - 1).reshape(-1)
+    U = O.links_from_labels(dims, lab)
+    assert not O.centre_charges(dims, lab).any()
+    c = O.cool(dims, U, 1, n_hits=3)
+    assert np.abs(c - U).max() < 1e-14
