@@ -1,0 +1,424 @@
+"""Benchmark of the vortex-field smoothing path on GB300.
+
+One step = the whole path on one synthetic 32^3 x 64 field: load the Z(3)
+labels, centrifuge preconditioning (omega = 0.02), 300 annealed over-improved
+stout sweeps (eps = -0.25, rho = 0.06) with the vortex-preservation test and
+FP64 re-unitarisation every 10 sweeps, then the action and the vortex check,
+in FP32 with 18-real links.  The input labels come from the library's cooled
+hot start (Haar SU(3), 20 MaxReTr cooling sweeps, Z(3) projection; seed 3 +
+rank).  The metric is link updates per second (4 V n_sweeps per step).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "link-updates/s at 32^3x64 FP32 vs FP64 at stated error; served p50/p99 latency"
+DIMS = (32, 32, 32, 64)
+N_SWEEPS = 300
+RHO, EPS, U0, OMEGA = 0.06, -0.25, 1.0, 0.02
+CENTRIFUGE_SEED = 1234
+N_COOL = 20
+REUNIT = 10
+# algorithmic bytes per link update of one colour-class launch (FP32, 18 reals):
+# every link of the field is read once (4 V links for V/4 updates = 16 reads
+# per update), the updated link written once, its reference label read once.
+BYTES_PER_UPDATE = {(1, 18): 17 * 72 + 1, (1, 12): 17 * 48 + 1, (0, 18): 17 * 144 + 1}
+FLOPS_PER_UPDATE_OVERIMPROVED = 65 * 216 + 600
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _dist_init():
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist, world, rank, local
+    return None, 1, 0, local
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, x, device):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _launches_per_step(n_sweeps, reunit):
+    # load_labels 1, centrifuge 1, 16 class updates per sweep, re-unitarisation,
+    # action (2 kernels), vortex check (2 kernels)
+    return 1 + 1 + 16 * n_sweeps + (n_sweeps // reunit if reunit else 0) + 2 + 2
+
+
+def run_ours(args):
+    import torch
+    dist, world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    from paper_2203_09764_gb300 import vs
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = vs.vs_create(local)
+    V = int(np.prod(DIMS))
+    n_links = 4 * V
+    seed = 3 + rank
+
+    # ---- input: cooled hot start, labels resident on the device ------------
+    gen = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK18, stream)
+    vs.vs_load_cooled(gen, seed, N_COOL)
+    labels_dev = torch.empty((4, V), dtype=torch.int8, device=dev)
+    vs.vs_read_labels(gen, labels_dev)
+    labels_host = torch.empty((4, V), dtype=torch.int8, pin_memory=True)
+    labels_host.copy_(labels_dev.cpu())
+    vs.vs_field_destroy(gen)
+
+    f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK18, stream)
+
+    def step(from_host=False, profile=False):
+        if from_host:
+            vs.vs_load_field(f, labels=labels_host)
+        else:
+            vs.vs_load_field(f, labels=labels_dev)
+        vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+        vs.vs_set_profiling(f, profile)
+        vs.vs_smooth(f, args.sweeps, RHO, EPS, U0, reunit_every=REUNIT, vortex_preserve=True)
+        S = vs.vs_action(f)
+        chk = vs.vs_vortex_check(f)
+        return S, chk
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region --------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    chain_ms, chain_launches = 0.0, 0
+    for _ in range(args.steps):
+        results.append(step(profile=True))
+        ms, nl = vs.vs_get_profile(f)
+        chain_ms += ms
+        chain_launches += nl
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    _barrier(dist)
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    t_ms = _max_over_ranks(dist, t_ms, dev)
+    ms_per_step = t_ms / args.steps
+    updates_per_step = n_links * args.sweeps
+    value = world * updates_per_step * args.steps / (t_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty((4, V, 3, 3), dtype=torch.complex128, pin_memory=True)
+        e2e_steps = max(1, min(args.steps, 3))
+        _barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            step(from_host=True)
+            vs.vs_read_field(f, out_host)
+        t_e2e = time.perf_counter() - t0
+        t_e2e = _max_over_ranks(dist, t_e2e, dev)
+        e2e = {"value": world * updates_per_step * e2e_steps / t_e2e, "unit": "link-updates/s",
+               "h2d_bytes_per_step": int(labels_host.numel()),
+               "d2h_bytes_per_step": int(out_host.numel() * 16 + 8 + 40), "steps": e2e_steps}
+    vs.vs_field_destroy(f)
+
+    line = {"metric": METRIC, "value": value, "unit": "link-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "32^3x64 cooled hot start (Haar SU(3) seed 3+rank, 20 MaxReTr "
+                                   "cooling sweeps, Z(3) projection); centrifuge w=0.02; "
+                                   "over-improved stout eps=-0.25 rho=0.06 u0=1, %d annealed sweeps "
+                                   "with vortex preservation, FP64 re-unitarisation every 10; "
+                                   "FP32 18-real links" % args.sweeps,
+                       "lattice": list(DIMS), "sweeps": args.sweeps, "precision": "fp32",
+                       "storage": "18-real", "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2: 604 MB field vs 129 MB L2"},
+            "clocks": clk, "e2e": e2e,
+            "gpu_launches": _launches_per_step(args.sweeps, REUNIT) * args.steps}
+
+    S_last, chk_last = results[-1]
+    line["result"] = {"action": S_last, "n_label_diff": chk_last["n_label_diff"],
+                      "n_charge_diff": chk_last["n_charge_diff"],
+                      "n_near_boundary": chk_last["n_near_boundary"]}
+
+    # ---- roofline of the dominant kernel (colour-class update) -------------
+    peaks, src = _measured_peaks()
+    per_launch_ms = chain_ms / max(chain_launches, 1)
+    units = V // 4
+    bpu = BYTES_PER_UPDATE[(1, 18)]
+    achieved = units * bpu / (per_launch_ms / 1e3) / 1e9
+    line["roofline"] = {"kernel": "k_subsweep<float,18,rect>", "bound": "hbm",
+                        "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                        "peak_source": src, "per_launch_ms": per_launch_ms,
+                        "bytes_per_update": bpu, "updates_per_launch": units,
+                        "achieved_tflops": units * FLOPS_PER_UPDATE_OVERIMPROVED
+                        / (per_launch_ms / 1e3) / 1e12}
+
+    # ---- FP64 plain path, bounded number of sweeps --------------------------
+    if not args.no_fp64:
+      try:
+        f64 = vs.vs_field_create(ctx, DIMS, vs.VS_FP64, vs.VS_LINK18, stream)
+        vs.vs_load_field(f64, labels=labels_dev)
+        vs.vs_centrifuge(f64, OMEGA, CENTRIFUGE_SEED)
+        vs.vs_smooth(f64, 1, RHO, EPS, U0, vortex_preserve=True)
+        torch.cuda.synchronize(dev)
+        n64 = args.fp64_sweeps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vs.vs_smooth(f64, n64, RHO, EPS, U0, vortex_preserve=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1)
+        v64 = n_links * n64 / (ms64 / 1e3)
+        line["fp64_plain"] = {"value": v64 * world, "unit": "link-updates/s", "sweeps": n64,
+                              "fp32_over_fp64": value / (v64 * world)}
+        vs.vs_field_destroy(f64)
+      except Exception as e:  # report, keep the main line
+        line["fp64_plain"] = {"error": repr(e)}
+
+    # ---- serving: continuous batching of a Poisson job mix -----------------
+    if not args.no_serve and rank == 0:
+        try:
+            line["serving"] = run_serving(vs, local, args)
+        except Exception as e:
+            line["serving"] = {"error": repr(e)}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(args, vs, ctx, stream)
+        except Exception as e:
+            line["cpu_baseline"] = {"error": repr(e)}
+
+    vs.vs_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_serving(vs, device, args):
+    import synth
+    jobs = synth.serving_jobs(n_jobs=args.serve_jobs, seed=99, rate_hz=args.serve_rate)
+    budget = 512 << 20
+    ctx = vs.vs_create(device, hbm_budget_bytes=budget, max_slots=8)
+    handles = []
+    t_start = time.perf_counter()
+    for j in jobs:
+        while time.perf_counter() - t_start < j["arrival_s"]:
+            time.sleep(0.0005)
+        job = vs.make_job(j["dims"], j["rho"], j["n_sweeps"], epsilon=EPS, seed=j["seed"],
+                          n_cool=N_COOL, omega=OMEGA, centrifuge_seed=CENTRIFUGE_SEED)
+        handles.append((vs.vs_submit(ctx, job), job, j))
+    lat, updates = [], 0
+    for t, job, j in handles:
+        r = vs.vs_poll(ctx, t, -1)
+        assert r["status"] == vs.VS_OK, r
+        lat.append(r["t_done_ms"] - r["t_submit_ms"])
+        updates += 4 * int(np.prod(j["dims"])) * j["n_sweeps"]
+    wall = time.perf_counter() - t_start
+    st = vs.vs_serve_stats_get(ctx)
+    vs.vs_destroy(ctx)
+    lat = np.array(lat)
+    return {"jobs": len(jobs), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "jobs_per_s": len(jobs) / wall,
+            "link_updates_per_s": updates / wall, "hbm_budget_bytes": budget,
+            "peak_bytes_in_use": st["peak_bytes_in_use"], "max_slots": 8,
+            "arrival_rate_hz": args.serve_rate,
+            "mix": "shapes {8^4, 12^3x24, 16^3x32, 24^3x48}, rho U[0.04,0.1], 50-300 sweeps, "
+                   "eps=-0.25, w=0.02, VP, FP32, Poisson arrivals (seed 99), job seeds 100-163"}
+
+
+def cpu_baseline(args, vs=None, ctx=None, stream=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: one
+    annealed sweep of the 32^3 x 64 field (8.4M link updates) from iid uniform
+    Z(3) labels (the cooled-and-projected hot start has uniform label marginals),
+    after the centrifuge.  Returns link-updates/s on the host cores."""
+    import oracle as O
+    import synth
+    V = int(np.prod(DIMS))
+    lab = synth.iid_labels(DIMS, 3, p0=1 / 3, p_plus=1 / 3)
+    Uc = O.centrifuge(DIMS, lab, OMEGA, CENTRIFUGE_SEED)
+    nt = O.max_threads()
+    t0 = time.perf_counter()
+    U1, rej = O.smooth(DIMS, Uc, lab, args.cpu_sweeps, RHO, eps=EPS, vp=True, nthreads=nt)
+    dt = time.perf_counter() - t0
+    out = {"value": 4 * V * args.cpu_sweeps / dt, "unit": "link-updates/s", "cores": nt,
+           "kind": "oracle",
+           "sample": "%d annealed over-improved sweep(s) of the 32^3x64 field from iid uniform "
+                     "Z(3) labels (seed 3) after the centrifuge, FP64, OpenMP over the sites of "
+                     "a colour class" % args.cpu_sweeps, "seconds": dt}
+    if vs is not None:
+        # error of the FP32 GPU path against the oracle on the same sample
+        f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK18, stream)
+        vs.vs_load_field(f, labels=lab)
+        vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+        st = vs.vs_smooth(f, args.cpu_sweeps, RHO, EPS, U0, vortex_preserve=True, stats=True,
+                          reunit_every=REUNIT)
+        Ug = vs.vs_read_field(f)
+        vs.vs_field_destroy(f)
+        out["fp32_max_link_err_vs_oracle"] = float(np.abs(Ug - U1).max())
+        out["reject_counts_equal"] = [s["n_reject"] for s in st] == list(rej)
+    return out
+
+
+def run_reference(args):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if world > 1 and rank != 0:
+        return
+    t0 = time.perf_counter()
+    for _ in range(min(args.warmup, 1)):
+        cpu_baseline(args)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args))
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": "link-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 4 * int(np.prod(DIMS)) * args.sweeps / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "32^3x64 over-improved stout eps=-0.25 rho=0.06, annealed, VP, "
+                                   "centrifuge w=0.02 (FP64 CPU oracle, timed on a bounded sample; "
+                                   "ms_per_step extrapolated to %d sweeps)" % args.sweeps,
+                       "lattice": list(DIMS), "sweeps": args.sweeps},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "link-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps", type=int, default=N_SWEEPS)
+    ap.add_argument("--fp64-sweeps", type=int, default=10)
+    ap.add_argument("--cpu-sweeps", type=int, default=1)
+    ap.add_argument("--serve-jobs", type=int, default=64)
+    ap.add_argument("--serve-rate", type=float, default=12.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

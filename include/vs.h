@@ -1,0 +1,266 @@
+/*
+ * vs.h -- C ABI of the GB300 vortex-field smoothing library (libvs.so).
+ *
+ * Method: Virgili, Kamleh & Leinweber, "Smoothing algorithms for projected
+ * center-vortex gauge fields", arXiv:2203.09764.  The library smooths a
+ * Z(3)-projected centre-vortex gauge field on one GPU:
+ *   load (Sec. I, Eqs. centre_project / centre_element)
+ *   -> centrifuge preconditioning (Sec. IV, Eqs. lambda_j / lambda_k)
+ *   -> annealed stout smoothing with standard or over-improved staples
+ *      (Sec. II.A Eqs. stout / generator, Sec. III Eq. over-improvement,
+ *       Sec. V.B annealed Euler Wilson flow) and the vortex-preservation
+ *      accept/reject test (Sec. VI)
+ *   -> vortex check and Wilson action (Sec. I, Sec. V).
+ *
+ * Conventions shared by every call:
+ *   dims[4] = {Lx, Ly, Lz, Lt}; every extent must be a positive multiple of 4
+ *     (the annealed schedule colours links by (2 x_mu + sum_{nu != mu} x_nu) mod 4).
+ *   Host link arrays: double [4][V][3][3][2] (direction major, then the
+ *     lexicographic site s = x + Lx*(y + Ly*(z + Lz*t)), then the row-major
+ *     3x3 matrix as (re, im) pairs).  Host label arrays: int8_t [4][V] in
+ *     {-1, 0, +1}, same ordering.
+ *   `where` selects whether a caller pointer is host memory (VS_HOST) or CUDA
+ *     device memory (VS_DEVICE) of the field's device.
+ *   The caller keeps ownership of every buffer it passes in; the library
+ *     copies what it needs before the call returns (host) or before work on
+ *     the field's stream that follows the call (device).
+ *   Every call returns a vs_status; on failure vs_last_error() describes it.
+ *     No C++ exception crosses this boundary.  Calls on one vs_field are not
+ *     thread safe; distinct fields may be used from distinct threads.
+ */
+#ifndef VS_H
+#define VS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vs_status;
+enum {
+    VS_OK = 0,
+    VS_EINVAL = 1,       /* bad argument; nothing was launched */
+    VS_ENOMEM = 2,       /* device or host allocation failed */
+    VS_EBUSY = 3,        /* serving queue is full */
+    VS_EAGAIN = 4,       /* result not ready (poll with timeout 0) */
+    VS_ETIMEDOUT = 5,    /* poll timed out */
+    VS_EDEVICE = 6,      /* CUDA error or device error word set */
+    VS_EUNSUPPORTED = 7, /* combination not built */
+    VS_ENOTFOUND = 8,    /* unknown ticket */
+    VS_ECANCELED = 9     /* job was cancelled (vs_result.status) */
+};
+
+enum { VS_FP64 = 0, VS_FP32 = 1 };            /* arithmetic and storage precision */
+enum { VS_LINK18 = 0, VS_LINK12 = 1 };        /* 18 reals, or rows 1-2 with row 3 rebuilt */
+enum { VS_ANNEALED = 0, VS_SIMULTANEOUS = 1 };
+enum { VS_HOST = 0, VS_DEVICE = 1 };
+
+typedef struct vs_ctx vs_ctx;
+typedef struct vs_field vs_field;
+
+/* Device allocator hooks: return a device pointer of at least `bytes` bytes
+ * (aligned to 256 bytes) or NULL; free_fn releases it. */
+typedef void *(*vs_alloc_fn)(size_t bytes, void *user);
+typedef void (*vs_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int32_t device;             /* CUDA device ordinal */
+    vs_alloc_fn alloc;          /* NULL: cudaMalloc */
+    vs_free_fn free_fn;         /* NULL: cudaFree */
+    void *alloc_user;
+    uint64_t hbm_budget_bytes;  /* serving admission cap on device bytes; 0 = no cap */
+    int32_t max_slots;          /* serving: jobs on the device at once; 0 -> 8 */
+    int32_t max_queue;          /* serving: waiting jobs before VS_EBUSY; 0 -> 1024 */
+} vs_options;
+
+/* Thread-local description of the last failure on this thread. */
+const char *vs_last_error(void);
+
+/* Library version and the device code architecture it was built for. */
+const char *vs_version(void);
+
+vs_status vs_create(const vs_options *opt, vs_ctx **out);
+void vs_destroy(vs_ctx *ctx);
+
+/* Allocate a field (links + resident reference labels) on the context's
+ * device.  stream: a cudaStream_t to run on, or NULL for a library-owned
+ * stream.  EINVAL: an extent not a positive multiple of 4, or an unknown
+ * precision/storage; EUNSUPPORTED: FP64 with 12-real storage. */
+vs_status vs_field_create(vs_ctx *ctx, const int32_t dims[4], int32_t precision,
+                          int32_t storage, void *stream, vs_field **out);
+void vs_field_destroy(vs_field *f);
+
+/* Load, Sec. I Eqs. (centre_project)/(centre_element): exactly one of
+ * links / labels is non-NULL.  With links, the reference labels n_mu(x) are the
+ * Z(3) sectors of arg Tr U of the given links; with labels, every link becomes
+ * exp(2 pi i n/3) I.  The labels stay resident as the vortex-preservation
+ * reference until the next load.  EINVAL: both or neither input, a label
+ * outside {-1,0,1} (device input is not scanned). */
+vs_status vs_load_field(vs_field *f, const double *links, const int8_t *labels, int32_t where);
+
+/* Hot start from a seed: every link an independent Haar SU(3) matrix, then
+ * n_cool sweeps of annealed MaxReTr cooling (Sec. III, alpha = 1, plaquette
+ * staples, three passes over the SU(2) subgroups), then projection of every
+ * link to its Z(3) element, which also becomes the reference labels.  This is
+ * the synthetic stand-in for a gauge-fixed Monte-Carlo ensemble member. */
+vs_status vs_load_cooled(vs_field *f, uint64_t seed, int32_t n_cool);
+
+/* Centrifuge preconditioning, Sec. IV: every link at once from the original
+ * labels; staple phase sigma = m 2pi/18 with integer m, a random pair (j,k)
+ * per link from SplitMix64 value (mu*V + s) of `seed` mod 3 selecting
+ * (1,2),(2,3),(3,1); lambda^j = lambda + delta, lambda^k = lambda - delta,
+ * delta = omega (sigma - lambda).  EINVAL unless 0 <= omega < 1/4 (the bound
+ * that keeps every label, Sec. IV.A). */
+vs_status vs_centrifuge(vs_field *f, double omega, uint64_t seed);
+
+typedef struct {
+    int32_t kind;                 /* VS_ANNEALED or VS_SIMULTANEOUS */
+    const double *rho_per_sweep;  /* host [n_sweeps] step sizes, or NULL for constant rho */
+    int32_t reunit_every;         /* FP32: re-unitarise (FP64 Gram-Schmidt) every k sweeps; 0 = never */
+    int32_t action_every;         /* record <S> in stats every k sweeps; 0 = never */
+} vs_anneal;
+
+typedef struct {
+    int64_t n_accept;             /* candidates written */
+    int64_t n_reject;             /* candidates refused by the vortex-preservation test */
+    int64_t n_fp64_exp;           /* FP32 mode: exponentials redone in FP64 (|rho Q| large) */
+    double action;                /* <S>/beta after the sweep, when recorded */
+    int32_t has_action;
+    int32_t pad;
+} vs_sweep_stats;
+
+/* n_sweeps of stout smoothing, Eqs. (stout)/(generator), with
+ * Sigma = c0 (plaquette staples) + c1 (rectangles), c0 = (5 - 2 eps)/3,
+ * c1 = (eps - 1)/(12 u0^2) (Eq. over-improvement; eps = 1 is standard).
+ * Annealed: for mu = 0..3, for colour c = 0..3, all links of that class at
+ * once, in place (Sec. III.A masked updates; Sec. V.B: Euler Wilson flow with
+ * step rho).  Simultaneous: every link from the previous sweep's field.
+ * vortex_preserve != 0: a candidate is written only if its Z(3) label equals
+ * the original reference label (Sec. VI).  sched may be NULL (annealed,
+ * constant rho, re-unitarise every 10 sweeps in FP32, no action).  stats:
+ * NULL, or [n_sweeps] filled before return (the call then waits for the
+ * device).  Without stats the call only enqueues.  EINVAL: n_sweeps < 0,
+ * non-finite rho/eps, u0 <= 0.  EDEVICE: CUDA error or device error word. */
+vs_status vs_smooth(vs_field *f, int32_t n_sweeps, double rho, double epsilon, double u0,
+                    const vs_anneal *sched, int32_t vortex_preserve, vs_sweep_stats *stats);
+
+/* One colour class (mu, colour) of the annealed schedule, as vs_smooth runs it. */
+vs_status vs_subsweep(vs_field *f, int32_t mu, int32_t colour, double rho, double epsilon,
+                      double u0, int32_t vortex_preserve);
+
+typedef struct {
+    int64_t n_links;
+    int64_t n_label_diff;         /* links whose current Z(3) label != reference */
+    int64_t n_charge_diff;        /* plaquettes whose centre charge != reference (Sec. I) */
+    int64_t n_near_boundary;      /* links with arg Tr U within 1e-5 rad of a sector edge */
+    double min_margin;            /* smallest angular distance of arg Tr U from a sector edge */
+} vs_vortex_report;
+
+/* Vortex-structure check of the current field against the reference. Synchronous. */
+vs_status vs_vortex_check(vs_field *f, vs_vortex_report *out);
+
+/* Mean Wilson action density <S>/beta, Sec. V: (1/V) sum_x 1/72 sum_{mu != nu}
+ * Re Tr(1 - P_munu(x)); products in the field precision, sums in FP64 with a
+ * fixed reduction order.  Synchronous. */
+vs_status vs_action(vs_field *f, double *mean_S);
+
+/* Copy out the current links (FP64, host layout above) or labels. */
+vs_status vs_read_field(vs_field *f, double *links_out, int32_t where);
+vs_status vs_read_labels(vs_field *f, int8_t *labels_out, int32_t where);     /* reference */
+vs_status vs_current_labels(vs_field *f, int8_t *labels_out, int32_t where);  /* of current links */
+
+/* Re-unitarise every link now (FP64 Gram-Schmidt of rows 1-2, row 3 = conj(r1 x r2)). */
+vs_status vs_reunitarise(vs_field *f);
+
+/* Wait for all work queued on the field's stream; EDEVICE on a device error. */
+vs_status vs_synchronize(vs_field *f);
+
+/* Device-time profile of the subsweep launches made by vs_smooth while
+ * profiling is on: total milliseconds of the colour-class update chains (CUDA
+ * events around each sweep's chain on the field's stream) and the number of
+ * class-update launches they contain. */
+vs_status vs_set_profiling(vs_field *f, int32_t on);
+vs_status vs_get_profile(vs_field *f, double *chain_ms, int64_t *n_launches);
+
+typedef struct {
+    int32_t dims[4];
+    int32_t precision, storage;
+    int64_t n_sites;
+    int64_t plane_stride;          /* elements between component planes */
+    int32_t n_components;          /* 18 or 12 stored reals per link */
+    int32_t pad;
+    void *links;                   /* device: [4][n_components][plane_stride] */
+    int8_t *labels;                /* device: [4][plane_stride] reference labels */
+    void *stream;
+} vs_field_desc;
+
+/* Device layout of a field.  Within a component plane the sites follow the
+ * lexicographic rows (y, z, t), and inside each x-row the sites are grouped
+ * by x mod 4: position (x mod 4) * (Lx/4) + x/4 (see vs_layout_index). */
+vs_status vs_field_describe(const vs_field *f, vs_field_desc *out);
+
+/* Position of site (x,y,z,t) inside a component plane. */
+int64_t vs_layout_index(const int32_t dims[4], const int32_t x[4]);
+
+/* Diagnostic: exp(X) for n traceless anti-Hermitian 3x3 matrices by the
+ * kernels' Cayley-Hamilton series, in the given precision.  X, E: host
+ * double [n][3][3][2]. */
+vs_status vs_debug_expm(vs_ctx *ctx, const double *X, int32_t n, int32_t precision, double *E);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of smoothing jobs                          */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t dims[4];
+    int32_t precision, storage;
+    const int8_t *labels;          /* host [4][V] reference labels, or NULL: vs_load_cooled(seed, n_cool) */
+    uint64_t seed;
+    int32_t n_cool;
+    int32_t vortex_preserve;
+    double omega;                  /* centrifuge angle; < 0 skips the centrifuge */
+    uint64_t centrifuge_seed;
+    double rho, epsilon, u0;
+    int32_t n_sweeps;
+    int32_t reunit_every;
+    double *links_out;             /* optional host [4][V][3][3][2], written before completion */
+} vs_job;
+
+typedef struct {
+    double action;                 /* <S>/beta of the smoothed field */
+    int64_t n_reject;              /* vortex-preservation rejections over all sweeps */
+    int64_t n_label_diff;          /* label differences after the last sweep */
+    double t_submit_ms, t_admit_ms, t_done_ms;  /* on the context's monotonic clock */
+    vs_status status;
+    int32_t pad;
+} vs_result;
+
+/* Queue a job (the library copies it, and its labels).  Never waits on the
+ * GPU.  EBUSY when max_queue jobs are waiting; EINVAL on bad parameters. */
+vs_status vs_submit(vs_ctx *ctx, const vs_job *job, int64_t *ticket);
+
+/* Result of a job: OK (and the ticket is retired), EAGAIN if not done and
+ * timeout_ms == 0, ETIMEDOUT after timeout_ms (< 0: wait without limit). */
+vs_status vs_poll(vs_ctx *ctx, int64_t ticket, int32_t timeout_ms, vs_result *out);
+
+/* Cancel a queued or running job; its slot and memory are released at the
+ * next sweep boundary.  ENOTFOUND for unknown or retired tickets. */
+vs_status vs_cancel(vs_ctx *ctx, int64_t ticket);
+
+typedef struct {
+    int64_t submitted, completed, cancelled, running, waiting;
+    uint64_t bytes_in_use, peak_bytes_in_use;
+} vs_serve_stats;
+
+vs_status vs_serve_stats_get(vs_ctx *ctx, vs_serve_stats *out);
+
+/* Milliseconds on the context's monotonic clock (the clock of vs_result). */
+double vs_now_ms(vs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VS_H */

@@ -1,0 +1,74 @@
+// vs_api_internal.h -- host-side state behind the opaque handles of vs.h.
+#pragma once
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/vs.h"
+#include "vs_internal.h"
+
+namespace vs {
+struct Serve;
+}
+
+struct vs_ctx {
+    vs_options opt;
+    std::chrono::steady_clock::time_point t0;
+    vs::Serve *serve = nullptr;      // owned; released by serve_shutdown
+    std::mutex serve_init_mu;
+};
+
+struct vs_field {
+    vs_ctx *ctx = nullptr;
+    vs::Geo g{};
+    int prec = VS_FP64;
+    int nc = 18;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool loaded = false;
+    void *U = nullptr;
+    int8_t *ref = nullptr;
+    int8_t *cur = nullptr;
+    double *partials = nullptr;
+    double *d_result = nullptr;
+    unsigned long long *d_counts = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    unsigned long long *sweep_counts = nullptr;
+    double *sweep_actions = nullptr;
+    int sweep_cap = 0;
+    int last_action_every = 0;
+    bool profiling = false;
+    double prof_ms = 0;
+    int64_t prof_launches = 0;
+    std::vector<cudaEvent_t> events;
+};
+
+namespace vs {
+
+vs_status fail(vs_status st, const char *fmt, ...);
+vs_status cuda_fail(cudaError_t e, const char *what);
+void *dev_alloc(vs_ctx *c, size_t bytes);
+void dev_free(vs_ctx *c, void *p);
+uint64_t field_footprint(const int32_t dims[4], int32_t precision, int32_t storage);
+
+// Enqueue n_sweeps on the field's stream.  want_stats: per-sweep counters and
+// actions into the field's stats buffers.  fixed_counters (optional): every
+// sweep adds its reject / FP64 counts into this one pair instead.
+vs_status smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double eps, double u0,
+                         const vs_anneal *sched, int32_t vp, bool want_stats,
+                         unsigned long long *fixed_counters = nullptr);
+
+void serve_shutdown(vs_ctx *c);
+
+}  // namespace vs

@@ -1,0 +1,273 @@
+// vs_device.cuh -- device-side SU(3) algebra, lattice geometry and field layout.
+//
+// Field layout in HBM (structure of arrays):
+//   links[mu][k][i]  T = float or double, k = 0..NC-1 real components
+//   (NC = 18: row-major 3x3 as re,im pairs; NC = 12: rows 0 and 1 only, row 2
+//   rebuilt as conj(row0 x row1) on load), i = site position in the plane.
+//   Site position: rows (y, z, t) in lexicographic order, and inside each
+//   x-row the sites grouped by x mod 4: i = row*Lx + (x & 3)*(Lx/4) + (x >> 2).
+//   For a colour class of the annealed schedule the updated sites of one
+//   row form contiguous runs of Lx/4, so a warp's loads of any plane are
+//   whole 32-byte sectors.
+//   labels[mu][i]    int8 reference Z(3) label of link (mu, i).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vs {
+
+struct Geo {
+    int L[4];       // Lx, Ly, Lz, Lt
+    int Q;          // Lx / 4
+    int V;          // sites
+    long long P;    // plane stride in elements
+};
+
+__host__ __device__ __forceinline__ int wrapc(int v, int L) {
+    v = v < 0 ? v + L : v;
+    return v >= L ? v - L : v;
+}
+
+struct Pt { int x0, x1, x2, x3; };
+
+// x + k * e_d with periodic wrap (|k| <= L)
+__device__ __forceinline__ Pt mv(const Geo &g, Pt p, int d, int k) {
+    if (d == 0) p.x0 = wrapc(p.x0 + k, g.L[0]);
+    else if (d == 1) p.x1 = wrapc(p.x1 + k, g.L[1]);
+    else if (d == 2) p.x2 = wrapc(p.x2 + k, g.L[2]);
+    else p.x3 = wrapc(p.x3 + k, g.L[3]);
+    return p;
+}
+
+__host__ __device__ __forceinline__ int sidx(const Geo &g, int x0, int x1, int x2, int x3) {
+    return ((x3 * g.L[2] + x2) * g.L[1] + x1) * g.L[0] + (x0 & 3) * g.Q + (x0 >> 2);
+}
+__device__ __forceinline__ int sidx(const Geo &g, const Pt &p) { return sidx(g, p.x0, p.x1, p.x2, p.x3); }
+
+__device__ __forceinline__ int lexidx(const Geo &g, const Pt &p) {
+    return p.x0 + g.L[0] * (p.x1 + g.L[1] * (p.x2 + g.L[2] * p.x3));
+}
+
+// site at plane position i
+__device__ __forceinline__ Pt site_of_index(const Geo &g, int i) {
+    Pt p;
+    int w = i % g.L[0];
+    int row = i / g.L[0];
+    p.x0 = 4 * (w % g.Q) + w / g.Q;
+    p.x1 = row % g.L[1];
+    row /= g.L[1];
+    p.x2 = row % g.L[2];
+    p.x3 = row / g.L[2];
+    return p;
+}
+
+__device__ __forceinline__ Pt site_of_lex(const Geo &g, int s) {
+    Pt p;
+    p.x0 = s % g.L[0]; s /= g.L[0];
+    p.x1 = s % g.L[1]; s /= g.L[1];
+    p.x2 = s % g.L[2];
+    p.x3 = s / g.L[2];
+    return p;
+}
+
+// Thread t (0 <= t < V/4) of colour class (mu, c): the class is the set of
+// sites with (2 x_mu + sum_{nu != mu} x_nu) mod 4 == c.
+//  mu != 0: every x-row holds Lx/4 class sites, x = 4a + b with
+//           b = (c - (x_mu + y + z + t)) mod 4 over the row's (y,z,t) coordinates.
+//  mu == 0: 2x = c - (y+z+t) mod 4 needs c - (y+z+t) even: half the rows hold
+//           Lx/2 class sites, x mod 4 in {b0, b0 + 2}.
+template <int MU>
+__device__ __forceinline__ Pt class_site(const Geo &g, int c, int t) {
+    Pt p;
+    const int Q = g.Q;
+    if (MU != 0) {
+        int a = t % Q;
+        int row = t / Q;
+        p.x1 = row % g.L[1];
+        row /= g.L[1];
+        p.x2 = row % g.L[2];
+        p.x3 = row / g.L[2];
+        int xm = MU == 1 ? p.x1 : (MU == 2 ? p.x2 : p.x3);
+        int b = (c - (p.x1 + p.x2 + p.x3 + xm)) & 3;
+        p.x0 = 4 * a + b;
+    } else {
+        int w = t % (2 * Q);
+        int row = t / (2 * Q);
+        int h = g.L[1] >> 1;
+        int j = row % h;
+        row /= h;
+        p.x2 = row % g.L[2];
+        p.x3 = row / g.L[2];
+        p.x1 = 2 * j + ((c - p.x2 - p.x3) & 1);
+        int b0 = ((c - (p.x1 + p.x2 + p.x3)) >> 1) & 1;
+        p.x0 = 4 * (w % Q) + b0 + 2 * (w / Q);
+    }
+    return p;
+}
+
+// --------------------------------------------------------------------------
+// 3x3 complex matrices in registers
+// --------------------------------------------------------------------------
+
+template <class T>
+struct M3 {
+    T re[9];
+    T im[9];
+};
+
+template <class T>
+__device__ __forceinline__ M3<T> m3_dag(const M3<T> &a) {
+    M3<T> r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            r.re[i * 3 + j] = a.re[j * 3 + i];
+            r.im[i * 3 + j] = -a.im[j * 3 + i];
+        }
+    return r;
+}
+
+// r = a * b.  Every entry is the same chain of fused multiply-adds started
+// from zero, so entries built from equal inputs come out bit-identical (a
+// product of matrices proportional to the identity stays exactly so).
+template <class T>
+__device__ __forceinline__ M3<T> m3_mul(const M3<T> &a, const M3<T> &b) {
+    M3<T> r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T sr = T(0), si = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sr = fma(a.re[i * 3 + k], b.re[k * 3 + j], sr);
+                sr = fma(-a.im[i * 3 + k], b.im[k * 3 + j], sr);
+                si = fma(a.re[i * 3 + k], b.im[k * 3 + j], si);
+                si = fma(a.im[i * 3 + k], b.re[k * 3 + j], si);
+            }
+            r.re[i * 3 + j] = sr;
+            r.im[i * 3 + j] = si;
+        }
+    return r;
+}
+
+// r += a * b
+template <class T>
+__device__ __forceinline__ void m3_madd(M3<T> &r, const M3<T> &a, const M3<T> &b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T sr = r.re[i * 3 + j], si = r.im[i * 3 + j];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sr = fma(a.re[i * 3 + k], b.re[k * 3 + j], sr);
+                sr = fma(-a.im[i * 3 + k], b.im[k * 3 + j], sr);
+                si = fma(a.re[i * 3 + k], b.im[k * 3 + j], si);
+                si = fma(a.im[i * 3 + k], b.re[k * 3 + j], si);
+            }
+            r.re[i * 3 + j] = sr;
+            r.im[i * 3 + j] = si;
+        }
+}
+
+// r = a * b^dagger
+template <class T>
+__device__ __forceinline__ M3<T> m3_mul_nd(const M3<T> &a, const M3<T> &b) {
+    return m3_mul(a, m3_dag(b));
+}
+
+// r = a^dagger * b
+template <class T>
+__device__ __forceinline__ M3<T> m3_mul_dn(const M3<T> &a, const M3<T> &b) {
+    return m3_mul(m3_dag(a), b);
+}
+
+template <class T>
+__device__ __forceinline__ void m3_zero(M3<T> &r) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { r.re[k] = T(0); r.im[k] = T(0); }
+}
+
+// r += s * a
+template <class T>
+__device__ __forceinline__ void m3_axpy(M3<T> &r, T s, const M3<T> &a) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { r.re[k] = fma(s, a.re[k], r.re[k]); r.im[k] = fma(s, a.im[k], r.im[k]); }
+}
+
+template <class T>
+__device__ __forceinline__ void m3_scale(M3<T> &r, T s) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { r.re[k] *= s; r.im[k] *= s; }
+}
+
+// --------------------------------------------------------------------------
+// Link load / store
+// --------------------------------------------------------------------------
+
+template <class T, int NC>
+__device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P, int mu, int i) {
+    const T *p = U + (long long)mu * NC * P + i;
+    M3<T> m;
+#pragma unroll
+    for (int k = 0; k < NC / 2; ++k) {
+        m.re[k] = __ldg(p + (2 * k) * P);
+        m.im[k] = __ldg(p + (2 * k + 1) * P);
+    }
+    if (NC == 12) {
+        // row 2 = conj(row 0 x row 1)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+            T cr = m.re[j1] * m.re[3 + j2] - m.im[j1] * m.im[3 + j2]
+                 - (m.re[j2] * m.re[3 + j1] - m.im[j2] * m.im[3 + j1]);
+            T ci = m.re[j1] * m.im[3 + j2] + m.im[j1] * m.re[3 + j2]
+                 - (m.re[j2] * m.im[3 + j1] + m.im[j2] * m.re[3 + j1]);
+            m.re[6 + j] = cr;
+            m.im[6 + j] = -ci;
+        }
+    }
+    return m;
+}
+
+template <class T, int NC>
+__device__ __forceinline__ void store_link(T *__restrict__ U, long long P, int mu, int i, const M3<T> &m) {
+    T *p = U + (long long)mu * NC * P + i;
+#pragma unroll
+    for (int k = 0; k < NC / 2; ++k) {
+        p[(2 * k) * P] = m.re[k];
+        p[(2 * k + 1) * P] = m.im[k];
+    }
+}
+
+// --------------------------------------------------------------------------
+// Z(3) label of a trace t = a + ib (sector of arg t, Sec. I Eq. centre_element)
+//   0  : a > 0 and b^2 < 3 a^2          (|arg| < pi/3)
+//  +1  : b > 0, or b == 0 and a < 0      (arg in [pi/3, pi])
+//  -1  : b < 0                           (arg in (-pi, -pi/3])
+//   0  : t == 0
+// --------------------------------------------------------------------------
+
+template <class T>
+__device__ __forceinline__ int z3_label(T a, T b) {
+    if (a > T(0) && b * b < T(3) * a * a) return 0;
+    if (b > T(0)) return 1;
+    if (b < T(0)) return -1;
+    return a < T(0) ? 1 : 0;
+}
+
+// --------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014), counter mode: value i of stream seed
+// --------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace vs

@@ -1,0 +1,577 @@
+// vs_kernels.cu -- load/read conversions, centrifuge, action, vortex check,
+// re-unitarisation, hot-start generation and the exponential diagnostic.
+#include <cmath>
+
+#include "vs_internal.h"
+#include "vs_stout.cuh"
+
+namespace vs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int nblocks(long long n, int threads = kThreads) { return (int)((n + threads - 1) / threads); }
+
+// ---------------------------------------------------------------------------
+// Load / read
+// ---------------------------------------------------------------------------
+
+// Z_mu(x) = exp(2 pi i n / 3) I, Sec. I Eq. (centre_project).  One thread per link.
+template <class T, int NC>
+__global__ void k_load_labels(Geo g, const int8_t *__restrict__ lab, T *U, int8_t *ref) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    int n = lab[l];
+    Pt p = site_of_lex(g, s);
+    int i = sidx(g, p);
+    double sn, cs;
+    sincospi(2.0 * n / 3.0, &sn, &cs);
+    M3<T> z;
+    m3_zero(z);
+    z.re[0] = z.re[4] = z.re[8] = T(cs);
+    z.im[0] = z.im[4] = z.im[8] = T(sn);
+    store_link<T, NC>(U, g.P, mu, i, z);
+    ref[(long long)mu * g.P + i] = (int8_t)n;
+}
+
+// Links from FP64 host layout; the reference label is the sector of arg Tr U of the FP64 input.
+template <class T, int NC>
+__global__ void k_load_links(Geo g, const double *__restrict__ in, T *U, int8_t *ref) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    Pt p = site_of_lex(g, s);
+    int i = sidx(g, p);
+    const double *q = in + l * 18;
+    M3<T> m;
+    double tr = 0, ti = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        m.re[k] = T(q[2 * k]);
+        m.im[k] = T(q[2 * k + 1]);
+    }
+    tr = q[0] + q[8] + q[16];
+    ti = q[1] + q[9] + q[17];
+    store_link<T, NC>(U, g.P, mu, i, m);
+    ref[(long long)mu * g.P + i] = (int8_t)z3_label<double>(tr, ti);
+}
+
+template <class T, int NC>
+__global__ void k_read_links(Geo g, const T *__restrict__ U, double *out) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    Pt p = site_of_lex(g, s);
+    M3<T> m = load_link<T, NC>(U, g.P, mu, sidx(g, p));
+    double *q = out + l * 18;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        q[2 * k] = double(m.re[k]);
+        q[2 * k + 1] = double(m.im[k]);
+    }
+}
+
+__global__ void k_read_labels(Geo g, const int8_t *__restrict__ ref, int8_t *out) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    out[l] = ref[(long long)mu * g.P + sidx(g, site_of_lex(g, s))];
+}
+
+template <class T, int NC>
+__global__ void k_current_labels(Geo g, const T *__restrict__ U, int8_t *out) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    M3<T> m = load_link<T, NC>(U, g.P, mu, sidx(g, site_of_lex(g, s)));
+    out[l] = (int8_t)z3_label<T>(m.re[0] + m.re[4] + m.re[8], m.im[0] + m.im[4] + m.im[8]);
+}
+
+// ---------------------------------------------------------------------------
+// Centrifuge preconditioning, Sec. IV
+// ---------------------------------------------------------------------------
+
+// m = sum_{nu != mu} [n_nu(x) + n_mu(x+nu) - n_nu(x+mu) - n_nu(x-nu) + n_mu(x-nu)
+// + n_nu(x-nu+mu)] so that sigma = m 2 pi / 18; delta = omega (sigma - lambda)
+// = omega pi (m - 6n) / 9.  Pair p = SplitMix64(seed, mu V + s) mod 3 picks
+// (j,k) = (0,1), (1,2), (2,0): phase j gets lambda + delta, phase k lambda - delta.
+template <class T, int NC>
+__global__ void k_centrifuge(Geo g, const int8_t *__restrict__ ref, double omega, uint64_t seed, T *U) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    Pt x = site_of_lex(g, s);
+    auto lab = [&](int d, const Pt &p) { return (int)ref[(long long)d * g.P + sidx(g, p)]; };
+    int m = 0;
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+        int nu = (mu + j) & 3;
+        Pt xpn = mv(g, x, nu, 1), xpm = mv(g, x, mu, 1), xmn = mv(g, x, nu, -1);
+        Pt xmnpm = mv(g, xmn, mu, 1);
+        m += lab(nu, x) + lab(mu, xpn) - lab(nu, xpm) - lab(nu, xmn) + lab(mu, xmn) + lab(nu, xmnpm);
+    }
+    int n = lab(mu, x);
+    double delta = omega * (double)(m - 6 * n) / 9.0;   // in units of pi
+    int pair = (int)(splitmix64(seed, (uint64_t)mu * (uint64_t)g.V + (uint64_t)s) % 3ull);
+    int jj = pair, kk = (pair + 1) % 3;
+    double ph[3];
+    ph[0] = ph[1] = ph[2] = 2.0 * n / 3.0;
+    ph[jj] += delta;
+    ph[kk] -= delta;
+    M3<T> z;
+    m3_zero(z);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double sn, cs;
+        sincospi(ph[k], &sn, &cs);
+        z.re[4 * k] = T(cs);
+        z.im[4 * k] = T(sn);
+    }
+    store_link<T, NC>(U, g.P, mu, sidx(g, x), z);
+}
+
+// ---------------------------------------------------------------------------
+// Wilson action, Sec. V: sum_x sum_{mu<nu} (3 - Re Tr P_munu(x)), FP64 sums
+// in a fixed order (block tree, then one block over the partials).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (ln == 0) sh[w] = v;
+    __syncthreads();
+    v = 0;
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        v = ln < nw ? sh[ln] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+template <class T, int NC>
+__global__ void __launch_bounds__(kThreads) k_action(Geo g, const T *__restrict__ U, double *partials) {
+    double acc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.V; i += gridDim.x * blockDim.x) {
+        Pt x = site_of_index(g, i);
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+            M3<T> Umu = load_link<T, NC>(U, g.P, mu, i);
+            Pt xm = mv(g, x, mu, 1);
+#pragma unroll
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                Pt xn = mv(g, x, nu, 1);
+                // P = (U_mu(x) U_nu(x+mu)) (U_nu(x) U_mu(x+nu))^dag
+                M3<T> X = m3_mul(Umu, load_link<T, NC>(U, g.P, nu, sidx(g, xm)));
+                M3<T> Y = m3_mul(load_link<T, NC>(U, g.P, nu, i), load_link<T, NC>(U, g.P, mu, sidx(g, xn)));
+                double re = 0;
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    re = fma((double)X.re[k], (double)Y.re[k], fma((double)X.im[k], (double)Y.im[k], re));
+                acc += 3.0 - re;
+            }
+        }
+    }
+    double b = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+__global__ void k_sum_partials(const double *__restrict__ partials, int n, double scale, double *out) {
+    double acc = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+    double b = block_sum(acc);
+    if (threadIdx.x == 0) *out = b * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Vortex check
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void count_warp(unsigned long long *ctr, bool pred) {
+    unsigned b = __ballot_sync(0xffffffffu, pred);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(ctr, (unsigned long long)__popc(b));
+}
+
+template <class T, int NC>
+__global__ void k_vortex_links(Geo g, const T *__restrict__ U, const int8_t *__restrict__ ref,
+                               int8_t *cur, unsigned long long *counts, unsigned long long *mbits) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool diff = false, near = false;
+    double margin = 1e300;
+    if (l < 4ll * g.V) {
+        int mu = (int)(l / g.V), i = (int)(l % g.V);
+        M3<T> m = load_link<T, NC>(U, g.P, mu, i);
+        T a = m.re[0] + m.re[4] + m.re[8], b = m.im[0] + m.im[4] + m.im[8];
+        int lab = z3_label<T>(a, b);
+        cur[(long long)mu * g.P + i] = (int8_t)lab;
+        diff = lab != ref[(long long)mu * g.P + i];
+        double arg = atan2((double)b + 0.0, (double)a);
+        const double pi3 = 1.0471975511965976;
+        margin = fmin(fmin(fabs(arg - pi3), fabs(arg + pi3)), 3.141592653589793 - fabs(arg));
+        near = margin < 1e-5;
+    }
+    count_warp(&counts[0], diff);
+    count_warp(&counts[2], near);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) margin = fmin(margin, __shfl_xor_sync(0xffffffffu, margin, o));
+    if ((threadIdx.x & 31) == 0 && margin < 1e300)
+        atomicMin(mbits, (unsigned long long)__double_as_longlong(margin));
+}
+
+// centre charge p = n_mu(x) + n_nu(x+mu) - n_mu(x+nu) - n_nu(x) mod 3 in {-1,0,1}
+__device__ __forceinline__ int charge(const Geo &g, const int8_t *lab, const Pt &x, int i, int mu, int nu) {
+    int p = lab[(long long)mu * g.P + i] + lab[(long long)nu * g.P + sidx(g, mv(g, x, mu, 1))]
+          - lab[(long long)mu * g.P + sidx(g, mv(g, x, nu, 1))] - lab[(long long)nu * g.P + i];
+    p = ((p % 3) + 3) % 3;
+    return p == 2 ? -1 : p;
+}
+
+__global__ void k_vortex_charges(Geo g, const int8_t *__restrict__ ref, const int8_t *__restrict__ cur,
+                                 unsigned long long *counts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nd = 0;
+    if (i < g.V) {
+        Pt x = site_of_index(g, i);
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = mu + 1; nu < 4; ++nu)
+                nd += charge(g, cur, x, i, mu, nu) != charge(g, ref, x, i, mu, nu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    if ((threadIdx.x & 31) == 0 && nd) atomicAdd(&counts[1], (unsigned long long)nd);
+}
+
+// ---------------------------------------------------------------------------
+// Re-unitarisation in FP64: r0 /= |r0|; r1 -= (r0^dag r1) r0; r1 /= |r1|;
+// r2 = conj(r0 x r1).
+// ---------------------------------------------------------------------------
+
+template <class T, int NC>
+__global__ void k_reunit(Geo g, T *U) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), i = (int)(l % g.V);
+    M3<T> m = load_link<T, NC>(U, g.P, mu, i);
+    double r[3][3], im[3][3];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b) { r[a][b] = m.re[3 * a + b]; im[a][b] = m.im[3 * a + b]; }
+    double n0 = 0;
+    for (int b = 0; b < 3; ++b) n0 += r[0][b] * r[0][b] + im[0][b] * im[0][b];
+    n0 = 1.0 / sqrt(n0);
+    for (int b = 0; b < 3; ++b) { r[0][b] *= n0; im[0][b] *= n0; }
+    double pr = 0, pi = 0;  // r0^dag r1
+    for (int b = 0; b < 3; ++b) {
+        pr += r[0][b] * r[1][b] + im[0][b] * im[1][b];
+        pi += r[0][b] * im[1][b] - im[0][b] * r[1][b];
+    }
+    for (int b = 0; b < 3; ++b) {
+        r[1][b] -= pr * r[0][b] - pi * im[0][b];
+        im[1][b] -= pr * im[0][b] + pi * r[0][b];
+    }
+    double n1 = 0;
+    for (int b = 0; b < 3; ++b) n1 += r[1][b] * r[1][b] + im[1][b] * im[1][b];
+    n1 = 1.0 / sqrt(n1);
+    for (int b = 0; b < 3; ++b) { r[1][b] *= n1; im[1][b] *= n1; }
+    for (int j = 0; j < 3; ++j) {
+        int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        double cr = r[0][j1] * r[1][j2] - im[0][j1] * im[1][j2] - (r[0][j2] * r[1][j1] - im[0][j2] * im[1][j1]);
+        double ci = r[0][j1] * im[1][j2] + im[0][j1] * r[1][j2] - (r[0][j2] * im[1][j1] + im[0][j2] * r[1][j1]);
+        r[2][j] = cr;
+        im[2][j] = -ci;
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) { m.re[3 * a + b] = T(r[a][b]); m.im[3 * a + b] = T(im[a][b]); }
+    store_link<T, NC>(U, g.P, mu, i, m);
+}
+
+// ---------------------------------------------------------------------------
+// Exponential diagnostic: E = exp(X), X traceless anti-Hermitian, via H = -iX
+// ---------------------------------------------------------------------------
+
+template <class T>
+__global__ void k_debug_expm(const double *__restrict__ X, int n, double *E) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double *x = X + 18ll * t;
+    // H_jk = -i X_jk -> re = Im X_jk, im = -Re X_jk
+    auto hre = [&](int j, int k) { return T(x[2 * (3 * j + k) + 1]); };
+    auto him = [&](int j, int k) { return T(-x[2 * (3 * j + k)]); };
+    bool f64;
+    M3<T> M = exp_iH<T>(hre(0, 0), hre(1, 1), hre(2, 2), hre(0, 1), him(0, 1), hre(0, 2), him(0, 2),
+                        hre(1, 2), him(1, 2), f64);
+    double *e = E + 18ll * t;
+    for (int k = 0; k < 9; ++k) { e[2 * k] = double(M.re[k]); e[2 * k + 1] = double(M.im[k]); }
+}
+
+// ---------------------------------------------------------------------------
+// Hot start and MaxReTr cooling (input generation)
+// ---------------------------------------------------------------------------
+
+// Haar SU(3) per link: 18 Gaussians by Box-Muller from SplitMix64 values
+// 18 l .. 18 l + 17 of `seed` (pair k: radius from value 2k, angle from 2k+1),
+// Z_jk = (g_{2(3j+k)} + i g_{2(3j+k)+1}) / sqrt 2, Gram-Schmidt on the columns
+// (QR with positive diag R: Haar U(3), Mezzadri 2007), then divide by the
+// principal cube root of det.
+template <class T, int NC>
+__global__ void k_haar(Geo g, uint64_t seed, T *U) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    double zr[9], zi[9];
+    const double inv53 = 1.0 / 9007199254740992.0;
+    for (int k = 0; k < 9; ++k) {
+        uint64_t c = (uint64_t)l * 18ull + 2ull * k;
+        double u1 = 1.0 - (double)(splitmix64(seed, c) >> 11) * inv53;
+        double u2 = (double)(splitmix64(seed, c + 1) >> 11) * inv53;
+        double rad = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        zr[k] = rad * cs * 0.7071067811865476;
+        zi[k] = rad * sn * 0.7071067811865476;
+    }
+    // Gram-Schmidt on columns c = 0, 1, 2 (entries (j, c) at index 3j + c)
+    for (int c = 0; c < 3; ++c) {
+        for (int p = 0; p < c; ++p) {
+            double pr = 0, pi = 0;  // <q_p, z_c> = sum conj(q_jp) z_jc
+            for (int j = 0; j < 3; ++j) {
+                pr += zr[3 * j + p] * zr[3 * j + c] + zi[3 * j + p] * zi[3 * j + c];
+                pi += zr[3 * j + p] * zi[3 * j + c] - zi[3 * j + p] * zr[3 * j + c];
+            }
+            for (int j = 0; j < 3; ++j) {
+                zr[3 * j + c] -= pr * zr[3 * j + p] - pi * zi[3 * j + p];
+                zi[3 * j + c] -= pr * zi[3 * j + p] + pi * zr[3 * j + p];
+            }
+        }
+        double nn = 0;
+        for (int j = 0; j < 3; ++j) nn += zr[3 * j + c] * zr[3 * j + c] + zi[3 * j + c] * zi[3 * j + c];
+        nn = 1.0 / sqrt(nn);
+        for (int j = 0; j < 3; ++j) { zr[3 * j + c] *= nn; zi[3 * j + c] *= nn; }
+    }
+    // det by expansion along row 0
+    auto cm = [](double ar, double ai, double br, double bi, double &rr, double &ri) {
+        rr = ar * br - ai * bi; ri = ar * bi + ai * br;
+    };
+    double dr = 0, di = 0;
+    for (int k = 0; k < 3; ++k) {
+        int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        double pr, pi, qr, qi, mr, mi;
+        cm(zr[3 + k1], zi[3 + k1], zr[6 + k2], zi[6 + k2], pr, pi);
+        cm(zr[3 + k2], zi[3 + k2], zr[6 + k1], zi[6 + k1], qr, qi);
+        cm(zr[k], zi[k], pr - qr, pi - qi, mr, mi);
+        dr += mr; di += mi;
+    }
+    double ph = atan2(di, dr) / 3.0;
+    double sn, cs;
+    sincos(-ph, &sn, &cs);
+    M3<T> m;
+    for (int k = 0; k < 9; ++k) {
+        m.re[k] = T(zr[k] * cs - zi[k] * sn);
+        m.im[k] = T(zr[k] * sn + zi[k] * cs);
+    }
+    store_link<T, NC>(U, g.P, mu, sidx(g, site_of_lex(g, s)), m);
+}
+
+// One colour class of annealed MaxReTr cooling (Sec. III, alpha = 1):
+// V = Sigma / 6; three passes over the SU(2) subgroups (0,1), (1,2), (0,2):
+// L = U V^dag, alpha = (L_pp + conj L_qq)/2, beta = (L_pq - conj L_qp)/2,
+// k = sqrt(|alpha|^2 + |beta|^2), T^c = [[conj alpha, -beta], [conj beta, alpha]] / k,
+// U <- T^c U.  k = 0 leaves the link unchanged.
+template <class T, int NC, int MU>
+__global__ void __launch_bounds__(128) k_cool(Geo g, int colour, T *U) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.V / 4) return;
+    Pt x = class_site<MU>(g, colour, t);
+    int i = sidx(g, x);
+    M3<T> sig = staple_sum<T, NC, false, MU>(g, U, x, T(1), T(0));
+    m3_scale(sig, T(1) / T(6));
+    M3<T> Vd = m3_dag(sig);
+    M3<T> u = load_link<T, NC>(U, g.P, MU, i);
+    const int sp[3] = {0, 1, 0}, sq[3] = {1, 2, 2};
+    for (int hit = 0; hit < 3; ++hit) {
+#pragma unroll
+        for (int sgi = 0; sgi < 3; ++sgi) {
+            const int p = sp[sgi], q = sq[sgi];
+            M3<T> L = m3_mul(u, Vd);
+            T ar = T(0.5) * (L.re[4 * p] + L.re[4 * q]), ai = T(0.5) * (L.im[4 * p] - L.im[4 * q]);
+            T br = T(0.5) * (L.re[3 * p + q] - L.re[3 * q + p]), bi = T(0.5) * (L.im[3 * p + q] + L.im[3 * q + p]);
+            T k = sqrt(ar * ar + ai * ai + br * br + bi * bi);
+            if (!(k > T(0))) continue;
+            T ik = T(1) / k;
+            // T^c block: [[conj a, -b], [conj b, a]] / k acting on rows p, q
+            T c00r = ar * ik, c00i = -ai * ik, c01r = -br * ik, c01i = -bi * ik;
+            T c10r = br * ik, c10i = -bi * ik, c11r = ar * ik, c11i = ai * ik;
+#pragma unroll
+            for (int col = 0; col < 3; ++col) {
+                T upr = u.re[3 * p + col], upi = u.im[3 * p + col];
+                T uqr = u.re[3 * q + col], uqi = u.im[3 * q + col];
+                u.re[3 * p + col] = c00r * upr - c00i * upi + c01r * uqr - c01i * uqi;
+                u.im[3 * p + col] = c00r * upi + c00i * upr + c01r * uqi + c01i * uqr;
+                u.re[3 * q + col] = c10r * upr - c10i * upi + c11r * uqr - c11i * uqi;
+                u.im[3 * q + col] = c10r * upi + c10i * upr + c11r * uqi + c11i * uqr;
+            }
+        }
+    }
+    store_link<T, NC>(U, g.P, MU, i, u);
+}
+
+// Z(3) projection of every link: reference label from arg Tr U, link -> exp(2 pi i n/3) I.
+template <class T, int NC>
+__global__ void k_project(Geo g, T *U, int8_t *ref) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), i = (int)(l % g.V);
+    M3<T> m = load_link<T, NC>(U, g.P, mu, i);
+    int n = z3_label<T>(m.re[0] + m.re[4] + m.re[8], m.im[0] + m.im[4] + m.im[8]);
+    double sn, cs;
+    sincospi(2.0 * n / 3.0, &sn, &cs);
+    M3<T> z;
+    m3_zero(z);
+    z.re[0] = z.re[4] = z.re[8] = T(cs);
+    z.im[0] = z.im[4] = z.im[8] = T(sn);
+    store_link<T, NC>(U, g.P, mu, i, z);
+    ref[(long long)mu * g.P + i] = (int8_t)n;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Dispatch
+// ---------------------------------------------------------------------------
+
+#define VS_DISPATCH(prec, nc, KERNEL, ...)                                          \
+    do {                                                                            \
+        if ((prec) == 0 && (nc) == 18) { KERNEL<double, 18>__VA_ARGS__; }           \
+        else if ((prec) == 1 && (nc) == 18) { KERNEL<float, 18>__VA_ARGS__; }       \
+        else if ((prec) == 1 && (nc) == 12) { KERNEL<float, 12>__VA_ARGS__; }       \
+        else return cudaErrorInvalidValue;                                          \
+    } while (0)
+
+cudaError_t launch_load_labels(int prec, int nc, const Geo &g, const int8_t *lab, void *U, int8_t *ref,
+                               cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_load_labels<double, 18><<<b, kThreads, 0, st>>>(g, lab, (double *)U, ref);
+    else if (nc == 18) k_load_labels<float, 18><<<b, kThreads, 0, st>>>(g, lab, (float *)U, ref);
+    else k_load_labels<float, 12><<<b, kThreads, 0, st>>>(g, lab, (float *)U, ref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_links(int prec, int nc, const Geo &g, const double *in, void *U, int8_t *ref,
+                              cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_load_links<double, 18><<<b, kThreads, 0, st>>>(g, in, (double *)U, ref);
+    else if (nc == 18) k_load_links<float, 18><<<b, kThreads, 0, st>>>(g, in, (float *)U, ref);
+    else k_load_links<float, 12><<<b, kThreads, 0, st>>>(g, in, (float *)U, ref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_links(int prec, int nc, const Geo &g, const void *U, double *out, cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_read_links<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, out);
+    else if (nc == 18) k_read_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    else k_read_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_labels(const Geo &g, const int8_t *ref, int8_t *out, cudaStream_t st) {
+    k_read_labels<<<nblocks(4ll * g.V), kThreads, 0, st>>>(g, ref, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_current_labels(int prec, int nc, const Geo &g, const void *U, int8_t *out, cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_current_labels<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, out);
+    else if (nc == 18) k_current_labels<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    else k_current_labels<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centrifuge(int prec, int nc, const Geo &g, const int8_t *ref, double omega, uint64_t seed,
+                              void *U, cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_centrifuge<double, 18><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (double *)U);
+    else if (nc == 18) k_centrifuge<float, 18><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (float *)U);
+    else k_centrifuge<float, 12><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (float *)U);
+    return cudaGetLastError();
+}
+
+int action_partials(const Geo &g) {
+    int b = nblocks(g.V);
+    return b < 1216 ? b : 1216;
+}
+
+cudaError_t launch_action(int prec, int nc, const Geo &g, const void *U, double *partials, double *out,
+                          cudaStream_t st) {
+    int b = action_partials(g);
+    if (prec == 0) k_action<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, partials);
+    else if (nc == 18) k_action<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, partials);
+    else k_action<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, partials);
+    // <S>/beta = (1/V) sum_x (2/72) sum_{mu<nu} (3 - Re Tr P)
+    k_sum_partials<<<1, 1024, 0, st>>>(partials, b, 2.0 / 72.0 / (double)g.V, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vortex(int prec, int nc, const Geo &g, const void *U, const int8_t *ref, int8_t *cur,
+                          unsigned long long *counts, unsigned long long *mbits, cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_vortex_links<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, ref, cur, counts, mbits);
+    else if (nc == 18) k_vortex_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits);
+    else k_vortex_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits);
+    k_vortex_charges<<<nblocks(g.V), kThreads, 0, st>>>(g, ref, cur, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_reunit<double, 18><<<b, kThreads, 0, st>>>(g, (double *)U);
+    else if (nc == 18) k_reunit<float, 18><<<b, kThreads, 0, st>>>(g, (float *)U);
+    else k_reunit<float, 12><<<b, kThreads, 0, st>>>(g, (float *)U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_expm(int prec, const double *X, int n, double *E, cudaStream_t st) {
+    if (prec == 0) k_debug_expm<double><<<nblocks(n), kThreads, 0, st>>>(X, n, E);
+    else k_debug_expm<float><<<nblocks(n), kThreads, 0, st>>>(X, n, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_haar(int prec, int nc, const Geo &g, uint64_t seed, void *U, cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_haar<double, 18><<<b, kThreads, 0, st>>>(g, seed, (double *)U);
+    else if (nc == 18) k_haar<float, 18><<<b, kThreads, 0, st>>>(g, seed, (float *)U);
+    else k_haar<float, 12><<<b, kThreads, 0, st>>>(g, seed, (float *)U);
+    return cudaGetLastError();
+}
+
+template <class T, int NC>
+static cudaError_t cool_tpl(const Geo &g, int mu, int colour, T *U, cudaStream_t st) {
+    int b = nblocks(g.V / 4, 128);
+    switch (mu) {
+        case 0: k_cool<T, NC, 0><<<b, 128, 0, st>>>(g, colour, U); break;
+        case 1: k_cool<T, NC, 1><<<b, 128, 0, st>>>(g, colour, U); break;
+        case 2: k_cool<T, NC, 2><<<b, 128, 0, st>>>(g, colour, U); break;
+        default: k_cool<T, NC, 3><<<b, 128, 0, st>>>(g, colour, U); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cool_class(int prec, int nc, const Geo &g, int mu, int colour, void *U, cudaStream_t st) {
+    if (prec == 0) return cool_tpl<double, 18>(g, mu, colour, (double *)U, st);
+    if (nc == 18) return cool_tpl<float, 18>(g, mu, colour, (float *)U, st);
+    return cool_tpl<float, 12>(g, mu, colour, (float *)U, st);
+}
+
+cudaError_t launch_project(int prec, int nc, const Geo &g, void *U, int8_t *ref, cudaStream_t st) {
+    int b = nblocks(4ll * g.V);
+    if (prec == 0) k_project<double, 18><<<b, kThreads, 0, st>>>(g, (double *)U, ref);
+    else if (nc == 18) k_project<float, 18><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
+    else k_project<float, 12><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
+    return cudaGetLastError();
+}
+
+}  // namespace vs

@@ -1,0 +1,36 @@
+// vs_sweep_inst.cuh -- instantiates the colour-class update kernel for one
+// (precision, storage) pair.  Included by vs_sweep_f18.cu, vs_sweep_f12.cu and
+// vs_sweep_d18.cu so the heavy instantiations compile in parallel.
+#pragma once
+
+#include "vs_internal.h"
+#include "vs_stout.cuh"
+
+namespace vs {
+
+template <class T, int NC>
+cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cudaStream_t st) {
+    const int threads = 128;
+    const int blocks = (p.n_threads + threads - 1) / threads;
+    if (blocks == 0) return cudaSuccess;
+#define VS_LAUNCH(R, M) k_subsweep<T, NC, R, M><<<blocks, threads, 0, st>>>(p)
+    if (rect) {
+        switch (mu) {
+            case 0: VS_LAUNCH(true, 0); break;
+            case 1: VS_LAUNCH(true, 1); break;
+            case 2: VS_LAUNCH(true, 2); break;
+            default: VS_LAUNCH(true, 3); break;
+        }
+    } else {
+        switch (mu) {
+            case 0: VS_LAUNCH(false, 0); break;
+            case 1: VS_LAUNCH(false, 1); break;
+            case 2: VS_LAUNCH(false, 2); break;
+            default: VS_LAUNCH(false, 3); break;
+        }
+    }
+#undef VS_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace vs

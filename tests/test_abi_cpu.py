@@ -1,0 +1,70 @@
+"""Host-only checks of the C ABI: the library builds, loads and exports every
+function include/vs.h declares; pure host helpers behave.  No GPU needed."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libvs():
+    from paper_2203_09764_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "vs.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(vs_[a-z0-9_]+)\s*\(", src))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_every_declared_function_is_exported(libvs):
+    names = _declared_functions()
+    assert len(names) >= 25
+    missing = [n for n in names if not hasattr(libvs, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_abi(libvs):
+    from paper_2203_09764_gb300 import vs
+    for n in _declared_functions():
+        assert hasattr(vs, n), n
+
+
+def test_layout_index_groups_x_by_residue(libvs):
+    from paper_2203_09764_gb300 import vs
+    dims = (8, 4, 4, 8)
+    seen = set()
+    for t in range(8):
+        for z in range(4):
+            for y in range(4):
+                for x in range(8):
+                    i = vs.vs_layout_index(dims, (x, y, z, t))
+                    row = y + 4 * (z + 4 * t)
+                    assert i == row * 8 + (x % 4) * 2 + x // 4
+                    seen.add(i)
+    assert seen == set(range(8 * 4 * 4 * 8))
+
+
+def test_version_and_error_string(libvs):
+    from paper_2203_09764_gb300 import vs
+    assert "sm_103a" in vs.vs_version()
+    assert isinstance(vs.vs_last_error(), str)
+
+
+def test_oracle_is_not_imported_by_the_product():
+    pkg = os.path.join(ROOT, "paper_2203_09764_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                with open(os.path.join(dirpath, fn)) as f:
+                    txt = f.read()
+                assert "import oracle" not in txt and "from oracle" not in txt, fn
+                assert "vs_oracle" not in txt, fn

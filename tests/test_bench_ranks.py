@@ -1,0 +1,55 @@
+"""The multi-rank plumbing of bench.py on CPU: two gloo ranks, barrier and
+max-over-ranks timing; the reference arm prints from rank 0 only."""
+
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+_CHILD = r"""
+import os, sys
+sys.path.insert(0, %(root)r)
+import bench
+dist, world, rank, local = bench._dist_init()
+assert world == 2 and dist is not None
+bench._barrier(dist)
+m = bench._max_over_ranks(dist, 1.5 + rank, "cpu")
+print("RANK%%d MAX %%.2f" %% (rank, m))
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_two_gloo_ranks_agree_on_max_time():
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
+        procs.append(subprocess.Popen([sys.executable, "-c", _CHILD % {"root": ROOT}], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=120) for p in procs]
+    for p, (o, e) in zip(procs, outs):
+        assert p.returncode == 0, e
+    assert "RANK0 MAX 2.50" in outs[0][0]
+    assert "RANK1 MAX 2.50" in outs[1][0]
+
+
+def test_reference_arm_is_silent_off_rank0():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""

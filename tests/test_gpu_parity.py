@@ -1,0 +1,231 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated per test): FP64 GPU vs oracle 1e-12 on links and 1e-12
+relative on the action (different exponential algorithm and summation order,
+rounding only); FP32 GPU after 200 sweeps within 1e-5 on links and 1e-6
+relative on the action; Z(3) labels, centre charges and the per-sweep
+vortex-preservation reject counts bit-exact.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests import lattice_np as L
+from tests.gpu_common import cooled_labels, gpu_pipeline, max_abs, oracle_pipeline
+
+pytestmark = pytest.mark.gpu
+
+vs = pytest.importorskip("paper_2203_09764_gb300.vs")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = vs.vs_create(0)
+    yield c
+    vs.vs_destroy(c)
+
+
+# --------------------------------------------------------------------------
+# Building blocks
+# --------------------------------------------------------------------------
+
+def _herm(rng, n, scale):
+    A = rng.normal(size=(n, 3, 3)) + 1j * rng.normal(size=(n, 3, 3))
+    H = 0.5 * (A + L.dag(A))
+    H -= np.trace(H, axis1=1, axis2=2)[:, None, None] / 3 * np.eye(3)
+    return H * (scale / np.linalg.norm(H, axis=(1, 2)))[:, None, None]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("fp32", 2e-7)])
+def test_exponential_matches_taylor_and_eigendecomposition(ctx, prec, tol):
+    rng = np.random.default_rng(5)
+    Hs = np.concatenate([_herm(rng, 200, s) for s in (1e-7, 1e-3, 0.05, 0.3, 0.9, 1.5, 3.0)])
+    # degenerate and near-degenerate spectra
+    for gap in (0.0, 1e-7, 1e-3):
+        W = synth.haar_su3(1, 9)[0]
+        Hs = np.concatenate([Hs, (W @ np.diag([0.2, 0.2 + gap, -0.4 - gap]) @ L.dag(W))[None]])
+    X = 1j * Hs
+    p = vs.VS_FP64 if prec == "fp64" else vs.VS_FP32
+    E = vs.vs_debug_expm(ctx, X, p)
+    Eeig = L.expm_eigh(X)
+    Etay = np.stack([O.expm(x) for x in X])
+    scale = np.maximum(1.0, np.linalg.norm(Hs, axis=(1, 2)))
+    assert (np.abs(E - Etay).max(axis=(1, 2)) / scale).max() < tol * 4
+    assert (np.abs(E - Eeig).max(axis=(1, 2)) / scale).max() < tol * 4
+    assert np.array_equal(vs.vs_debug_expm(ctx, np.zeros((1, 3, 3)), p)[0], np.eye(3))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_load_and_centrifuge_match_oracle(ctx, prec):
+    p = vs.VS_FP64 if prec == "fp64" else vs.VS_FP32
+    for dims, seed in [((4, 4, 4, 4), 1), ((8, 4, 12, 8), 2)]:
+        lab = synth.iid_labels(dims, seed)
+        f = vs.vs_field_create(ctx, dims, p, vs.VS_LINK18)
+        vs.vs_load_field(f, labels=lab)
+        assert np.array_equal(vs.vs_read_labels(f), lab)
+        Z = vs.vs_read_field(f)
+        assert max_abs(Z, O.links_from_labels(dims, lab)) < (1e-15 if prec == "fp64" else 1e-7)
+        vs.vs_centrifuge(f, 0.02, 1234)
+        U = vs.vs_read_field(f)
+        Uo = O.centrifuge(dims, lab, 0.02, 1234)
+        assert max_abs(U, Uo) < (1e-14 if prec == "fp64" else 1e-7)
+        assert np.array_equal(vs.vs_current_labels(f), lab)
+        assert vs.vs_vortex_check(f)["n_label_diff"] == 0
+        vs.vs_field_destroy(f)
+
+
+def test_load_links_and_labels_from_fp64_input(ctx):
+    dims = (4, 8, 4, 4)
+    U = synth.haar_field(dims, 3)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, links=U)
+    assert np.array_equal(vs.vs_read_field(f), U)
+    assert np.array_equal(vs.vs_read_labels(f), O.labels(dims, U))
+    vs.vs_field_destroy(f)
+
+
+def test_action_and_vortex_check_match_oracle(ctx):
+    dims = (8, 4, 4, 8)
+    U = synth.haar_field(dims, 4)
+    lab = synth.iid_labels(dims, 5)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, links=U)
+    assert abs(vs.vs_action(f) - O.action(dims, U)) < 1e-13
+    vs.vs_field_destroy(f)
+    # vortex check: reference labels from a pure Z(3) field, then compare with
+    # the labels of a different Z(3) field loaded over it -> counts from the oracle
+    Z = O.links_from_labels(dims, lab)
+    lab2 = lab.copy()
+    lab2[1, ::7] = ((lab2[1, ::7] + 2) % 3) - 1
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=lab)
+    chk = vs.vs_vortex_check(f)
+    assert chk["n_label_diff"] == 0 and chk["n_charge_diff"] == 0
+    assert abs(vs.vs_action(f) - O.action(dims, Z)) < 1e-13
+    vs.vs_field_destroy(f)
+    ref = O.vortex_check(dims, O.links_from_labels(dims, lab2), lab)
+    assert ref["n_label_diff"] == np.count_nonzero(lab2 != lab)
+    assert ref["n_charge_diff"] > 0
+
+
+# --------------------------------------------------------------------------
+# Smoothing parity
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("eps", [1.0, -0.25])
+def test_pure_z3_field_is_unchanged(ctx, prec, eps):
+    # Sec. II.A: Q = 0 on a vortex field; the kernels return it bit for bit.
+    dims = (8, 8, 4, 4)
+    lab = synth.iid_labels(dims, 1)
+    p = vs.VS_FP64 if prec == "fp64" else vs.VS_FP32
+    r = gpu_pipeline(vs, ctx, dims, lab, None, 0, 3, 0.1, eps, precision=p, reunit_every=0)
+    f = vs.vs_field_create(ctx, dims, p, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=lab)
+    Z = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    assert np.array_equal(r["U"], Z)
+    assert all(s["n_reject"] == 0 for s in r["stats"])
+
+
+def test_workload_4x4_pure_vortex_fp64(ctx):
+    """4^4 pure Z(3) field, P(0)=0.7, seed 1; centrifuge w=0.02 (seed 1234);
+    10 standard stout sweeps rho=0.1 with vortex preservation; FP64."""
+    dims = (4, 4, 4, 4)
+    lab = synth.iid_labels(dims, 1)
+    Uo, rej = oracle_pipeline(dims, lab, 0.02, 1234, 10, 0.1, 1.0)
+    r = gpu_pipeline(vs, ctx, dims, lab, 0.02, 1234, 10, 0.1, 1.0)
+    assert max_abs(r["U"], Uo) < 1e-12
+    assert [s["n_reject"] for s in r["stats"]] == list(rej)
+    assert np.array_equal(r["labels"], O.labels(dims, Uo))
+    assert abs(r["action"] - O.action(dims, Uo)) < 1e-12 * O.action(dims, Uo)
+    assert r["check"]["n_label_diff"] == 0 and r["check"]["n_charge_diff"] == 0
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (4, 8, 12, 16)])
+def test_overimproved_vp_fp64_on_cooled_input(ctx, dims):
+    lab = cooled_labels(dims, 2)
+    Uo, rej = oracle_pipeline(dims, lab, 0.02, 1234, 20, 0.06, -0.25)
+    r = gpu_pipeline(vs, ctx, dims, lab, 0.02, 1234, 20, 0.06, -0.25)
+    assert max_abs(r["U"], Uo) < 1e-12
+    assert [s["n_reject"] for s in r["stats"]] == list(rej)
+    assert abs(r["action"] / O.action(dims, Uo) - 1) < 1e-12
+
+
+def test_large_steps_exercise_rejections_fp64(ctx):
+    dims = (8, 4, 8, 4)
+    lab = synth.iid_labels(dims, 13)
+    Uo, rej = oracle_pipeline(dims, lab, 0.02, 1234, 6, 0.3, -0.25)
+    assert rej.sum() > 0
+    r = gpu_pipeline(vs, ctx, dims, lab, 0.02, 1234, 6, 0.3, -0.25)
+    assert [s["n_reject"] for s in r["stats"]] == list(rej)
+    # rounding-level differences (the two exponentials differ in the last bits)
+    # grow by the Lipschitz factor of the update, ~(1 + rho |dQ/dU|) per sweep:
+    # at rho = 0.3 that is a few per sweep, so allow 1e-11 after 6 sweeps.
+    assert max_abs(r["U"], Uo) < 1e-11
+
+
+@pytest.mark.parametrize("kind", ["annealed", "simultaneous"])
+@pytest.mark.parametrize("eps", [1.0, -0.25])
+def test_full_su3_field_parity(ctx, kind, eps):
+    """A general (non-diagonal) SU(3) field exercises every entry of the staple
+    products: a cooled Haar field, VP off."""
+    dims = (4, 8, 4, 8)
+    U = O.cool(dims, synth.haar_field(dims, 17), 3)
+    sched = O.ANNEALED if kind == "annealed" else O.SIMULTANEOUS
+    Uo, _ = O.smooth(dims, U, None, 3, 0.08, eps=eps, schedule=sched, vp=False)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, links=U)
+    vs.vs_smooth(f, 3, 0.08, eps, vortex_preserve=False,
+                 kind=vs.VS_ANNEALED if kind == "annealed" else vs.VS_SIMULTANEOUS)
+    Ug = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    assert max_abs(Ug, Uo) < 1e-12
+
+
+@pytest.mark.parametrize("storage", ["link18", "link12"])
+def test_fp32_200_sweeps_within_target(ctx, storage):
+    """FP32 mode after 200 over-improved annealed sweeps with VP: links within
+    1e-5 of the FP64 oracle, action within 1e-6 relative, labels and per-sweep
+    reject counts identical."""
+    dims = (8, 8, 8, 8)
+    lab = cooled_labels(dims, 2)
+    Uo, rej = oracle_pipeline(dims, lab, 0.02, 1234, 200, 0.06, -0.25)
+    st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
+    r = gpu_pipeline(vs, ctx, dims, lab, 0.02, 1234, 200, 0.06, -0.25, precision=vs.VS_FP32,
+                     storage=st)
+    err = max_abs(r["U"], Uo)
+    assert err < 1e-5, err
+    assert abs(r["action"] / O.action(dims, Uo) - 1) < 1e-6
+    assert np.array_equal(r["labels"], O.labels(dims, Uo))
+    assert [s["n_reject"] for s in r["stats"]] == list(rej)
+
+
+def test_subsweep_matches_single_link_oracle(ctx):
+    """One colour class on a full SU(3) field: every updated link equals the
+    oracle's exp(rho Q) U from the field before the launch; others untouched."""
+    dims = (8, 4, 4, 8)
+    U = O.cool(dims, synth.haar_field(dims, 23), 2)
+    c0, c1 = O.overimproved_coeffs(-0.25)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, links=U)
+    mu, col = 2, 3
+    vs.vs_subsweep(f, mu, col, 0.07, -0.25, 1.0, False)
+    Ug = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    V = int(np.prod(dims))
+    n_upd = 0
+    for s in range(V):
+        x = np.unravel_index(s, dims[::-1])[::-1]
+        for m in range(4):
+            if m == mu and O.colour(dims, mu, x) == col:
+                S = O.staple_sum(dims, U, mu, x, c0, c1)
+                Q = O.stout_generator(S @ L.dag(U[mu, s]))
+                ref = O.expm(0.07 * Q) @ U[mu, s]
+                assert np.abs(Ug[mu, s] - ref).max() < 1e-13
+                n_upd += 1
+            else:
+                assert np.array_equal(Ug[m, s], U[m, s])
+    assert n_upd == V // 4
