@@ -11,7 +11,7 @@ import subprocess
 import numpy as np
 
 __all__ = [
-    "build_oracle", "lib", "max_threads",
+    "build_oracle", "lib", "max_threads", "use_library", "compile_variant", "source",
     "label_matrix", "labels", "links_from_labels", "splitmix64", "centrifuge_pair",
     "centrifuge", "overimproved_coeffs", "staple_sum", "expm", "stout_generator",
     "colour", "smooth", "action", "centre_charges", "vortex_check", "gauge_transform",
@@ -41,41 +41,81 @@ def build_oracle(force=False):
     return _OUT
 
 
+def _bind(path):
+    L = ctypes.CDLL(path)
+    _declare(L)
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = build_oracle()
-        L = ctypes.CDLL(path)
-        P = ctypes.c_void_p
-        i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
-        sig = {
-            "or_label_matrix": (ctypes.c_int, [P]),
-            "or_labels": (ctypes.c_int, [P, P, P, P]),
-            "or_links_from_labels": (ctypes.c_int, [P, P, P]),
-            "or_splitmix64": (u64, [u64, u64]),
-            "or_centrifuge_pair": (ctypes.c_int, [u64, ctypes.c_long, ctypes.c_int, ctypes.c_long]),
-            "or_centrifuge": (ctypes.c_int, [P, P, dbl, u64, P, P]),
-            "or_overimproved_coeffs": (None, [dbl, dbl, P, P]),
-            "or_staple_sum": (ctypes.c_int, [P, P, ctypes.c_int, P, dbl, dbl, P]),
-            "or_expm": (ctypes.c_int, [P, P]),
-            "or_stout_generator": (ctypes.c_int, [P, P]),
-            "or_colour": (ctypes.c_int, [P, ctypes.c_int, P]),
-            "or_smooth": (ctypes.c_int, [P, P, P, ctypes.c_int, P, dbl, dbl,
-                                         ctypes.c_int, ctypes.c_int, P, ctypes.c_int]),
-            "or_action": (ctypes.c_int, [P, P, P, P]),
-            "or_centre_charges": (ctypes.c_int, [P, P, P]),
-            "or_vortex_check": (ctypes.c_int, [P, P, P, P, P, P]),
-            "or_gauge_transform": (ctypes.c_int, [P, P, P]),
-            "or_cool": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-            "or_max_threads": (ctypes.c_int, []),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        del i32, i64
-        _lib = L
+        _lib = _bind(build_oracle())
     return _lib
+
+
+class use_library:
+    """Context manager: route every oracle call through another build of
+    vs_oracle.c (the mutation tests load deliberately broken copies)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _bind(self.path)
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def compile_variant(src_text, out_path):
+    """Compile a modified oracle source (same flags as the real build)."""
+    src = out_path[:-3] + ".c"
+    with open(src, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           "-ffp-contract=off", "-fcx-limited-range", "-o", out_path, src, "-lm"])
+    return out_path
+
+
+def source():
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _declare(L):
+    P = ctypes.c_void_p
+    u64, dbl = ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "or_label_matrix": (ctypes.c_int, [P]),
+        "or_labels": (ctypes.c_int, [P, P, P, P]),
+        "or_links_from_labels": (ctypes.c_int, [P, P, P]),
+        "or_splitmix64": (u64, [u64, u64]),
+        "or_centrifuge_pair": (ctypes.c_int, [u64, ctypes.c_long, ctypes.c_int, ctypes.c_long]),
+        "or_centrifuge": (ctypes.c_int, [P, P, dbl, u64, P, P]),
+        "or_overimproved_coeffs": (None, [dbl, dbl, P, P]),
+        "or_staple_sum": (ctypes.c_int, [P, P, ctypes.c_int, P, dbl, dbl, P]),
+        "or_expm": (ctypes.c_int, [P, P]),
+        "or_stout_generator": (ctypes.c_int, [P, P]),
+        "or_colour": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "or_smooth": (ctypes.c_int, [P, P, P, ctypes.c_int, P, dbl, dbl,
+                                     ctypes.c_int, ctypes.c_int, P, ctypes.c_int]),
+        "or_action": (ctypes.c_int, [P, P, P, P]),
+        "or_centre_charges": (ctypes.c_int, [P, P, P]),
+        "or_vortex_check": (ctypes.c_int, [P, P, P, P, P, P]),
+        "or_gauge_transform": (ctypes.c_int, [P, P, P]),
+        "or_cool": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "or_max_threads": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
 
 
 def _p(a):

@@ -264,6 +264,25 @@ def test_centrifuge_closed_forms():
     srt = np.sort(dev, axis=-1)
     assert np.allclose(srt[..., 1], 0, atol=1e-14)
     assert np.allclose(np.abs(srt[..., 0]), np.abs(lamminus), atol=1e-14)
+    # sigma is the mean non-compact phase of the six staple paths (+nu +mu -nu and
+    # -nu +mu +nu), walked link by link over the label phases lambda = 2 pi n / 3
+    lam = (2 * np.pi / 3) * lab.astype(float).reshape((4,) + L.lat_shape(dims))
+    e = np.eye(4, dtype=int)
+    for mu in range(4):
+        tot = 0.0
+        for nu in range(4):
+            if nu == mu:
+                continue
+            for sg in (1, -1):
+                off = np.zeros(4, dtype=int)
+                for d, st in ((nu, sg), (mu, 1), (nu, -sg)):
+                    if st > 0:
+                        tot = tot + np.roll(lam[d], tuple(-off[::-1]), axis=(0, 1, 2, 3))
+                        off = off + e[d]
+                    else:
+                        off = off - e[d]
+                        tot = tot - np.roll(lam[d], tuple(-off[::-1]), axis=(0, 1, 2, 3))
+        assert np.allclose(sigma[mu], (tot / 6).reshape(-1), atol=1e-13)
     # labels are preserved (omega < 1/4, condition w|m - 6n| < 6)
     assert np.array_equal(O.labels(dims, U), lab)
     assert np.all(omega * np.abs(m - 6 * n) < 6)
@@ -479,6 +498,14 @@ def test_vortex_preservation_keeps_original_labels():
     assert chk["n_label_diff"] == 0 and chk["n_charge_diff"] == 0
     outn, _ = O.smooth(dims, U0, lab, 5, 0.5, eps=-0.25, vp=False)
     assert O.vortex_check(dims, outn, lab)["n_label_diff"] > 0
+    # the test is against the ORIGINAL labels (Sec. VI): starting from a field
+    # whose labels have drifted, a VP sweep only writes candidates carrying the
+    # original label, so every link is either unchanged or back in its sector
+    back, rej2 = O.smooth(dims, outn, lab, 1, 0.05, eps=-0.25, vp=True)
+    lb = O.labels(dims, back)
+    unchanged = np.all(back == outn, axis=(2, 3))
+    assert np.all(unchanged | (lb == lab))
+    assert rej2.sum() > 0 and np.any(~unchanged)
 
 
 # --------------------------------------------------------------------------
