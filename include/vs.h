@@ -188,10 +188,15 @@ typedef struct {
     int32_t dims[4];
     int32_t precision, storage;
     int64_t n_sites;
-    int64_t plane_stride;          /* elements between component planes */
-    int32_t n_components;          /* 18 or 12 stored reals per link */
+    int64_t plane_stride;          /* P: sites per vector plane */
+    int32_t n_components;          /* NC: 18 or 12 stored reals per link */
     int32_t pad;
-    void *links;                   /* device: [4][n_components][plane_stride] */
+    void *links;                   /* device: direction mu at element mu*NC*P, split into
+                                      vector planes: FP32 18 reals = 4 float4 planes
+                                      (complex entries 0-1, 2-3, 4-5, 6-7) + 1 float2 plane
+                                      (entry 8); FP32 12 reals = 3 float4 planes; FP64 =
+                                      9 double2 planes; a plane of w reals per site starts
+                                      at (reals before it)*P, site i at w*i inside it */
     int8_t *labels;                /* device: [4][plane_stride] reference labels */
     void *stream;
 } vs_field_desc;
@@ -203,6 +208,10 @@ vs_status vs_field_describe(const vs_field *f, vs_field_desc *out);
 
 /* Position of site (x,y,z,t) inside a component plane. */
 int64_t vs_layout_index(const int32_t dims[4], const int32_t x[4]);
+
+/* Number of kernels the library has launched directly in this process (CUDA
+ * graph replays of the serving loop are not counted). */
+int64_t vs_kernel_launches(void);
 
 /* Diagnostic: exp(X) for n traceless anti-Hermitian 3x3 matrices by the
  * kernels' Cayley-Hamilton series, in the given precision.  X, E: host

@@ -104,7 +104,7 @@ def _declare(L):
         "or_stout_generator": (ctypes.c_int, [P, P]),
         "or_colour": (ctypes.c_int, [P, ctypes.c_int, P]),
         "or_smooth": (ctypes.c_int, [P, P, P, ctypes.c_int, P, dbl, dbl,
-                                     ctypes.c_int, ctypes.c_int, P, ctypes.c_int]),
+                                     ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P]),
         "or_action": (ctypes.c_int, [P, P, P, P]),
         "or_centre_charges": (ctypes.c_int, [P, P, P]),
         "or_vortex_check": (ctypes.c_int, [P, P, P, P, P, P]),
@@ -223,8 +223,9 @@ def colour(dims, mu, x):
 
 
 def smooth(dims, links, ref_labels, n_sweeps, rho, eps=1.0, u0=1.0,
-           schedule=ANNEALED, vp=True, nthreads=None):
-    """n_sweeps of stout smoothing on a copy of ``links``; returns (links, n_reject)."""
+           schedule=ANNEALED, vp=True, nthreads=None, diagnostics=False):
+    """n_sweeps of stout smoothing on a copy of ``links``; returns (links, n_reject),
+    plus (candidate margins, rejected mask) of the last sweep with diagnostics=True."""
     d = _dims(dims)
     U = np.array(links, dtype=np.complex128, order="C", copy=True)
     if np.isscalar(rho):
@@ -235,8 +236,15 @@ def smooth(dims, links, ref_labels, n_sweeps, rho, eps=1.0, u0=1.0,
     ref = None if ref_labels is None else np.ascontiguousarray(ref_labels, dtype=np.int8)
     rej = np.zeros(max(n_sweeps, 1), dtype=np.int64)
     nt = max_threads() if nthreads is None else int(nthreads)
+    V = U.size // 36
+    cm = np.full((4, V), np.nan) if diagnostics else None
+    rj = np.zeros((4, V), dtype=np.int8) if diagnostics else None
     _check(lib().or_smooth(_p(d), _p(U), _p(ref) if ref is not None else None, n_sweeps,
-                           _p(rho), eps, u0, schedule, 1 if vp else 0, _p(rej), nt), "smooth")
+                           _p(rho), eps, u0, schedule, 1 if vp else 0, _p(rej), nt,
+                           _p(cm) if diagnostics else None, _p(rj) if diagnostics else None),
+           "smooth")
+    if diagnostics:
+        return U, rej[:n_sweeps], cm, rj
     return U, rej[:n_sweeps]
 
 

@@ -414,10 +414,13 @@ enum { OR_ANNEALED = 0, OR_SIMULTANEOUS = 1 };
  *                accepted only if its label equals the original one (Sec. VI).
  *   n_reject     optional [n_sweeps] rejected-candidate counts.
  *   nthreads     1 = strictly sequential; >1 runs the sites of one colour
- *                class concurrently (they are independent by construction). */
+ *                class concurrently (they are independent by construction).
+ *   cand_margin  optional [4][V]: angular distance of arg Tr of each link's
+ *                last candidate from the nearest sector edge (last sweep).
+ *   rejected     optional [4][V]: 1 where the last sweep rejected the candidate. */
 int or_smooth(const int32_t dims[4], double *links, const int8_t *ref_labels, int n_sweeps,
               const double *rho, double eps, double u0, int schedule, int vp,
-              int64_t *n_reject, int nthreads) {
+              int64_t *n_reject, int nthreads, double *cand_margin, int8_t *rejected) {
     lattice g;
     if (lat_init(&g, dims)) return -1;
     if (n_sweeps < 0) return -2;
@@ -451,8 +454,12 @@ int or_smooth(const int32_t dims[4], double *links, const int8_t *ref_labels, in
                         if (staple_sum(&g, U, mu, x, c0, c1, &S)) { err |= 1; continue; }
                         mat3 Ux = link_get(&g, U, mu, sites[i]);
                         mat3 Un = stout_candidate(&S, &Ux, rho[sw]);
-                        if (vp && label_of_trace(m_trace(&Un)) != ref_labels[(long)mu * g.V + sites[i]]) {
+                        const long li = (long)mu * g.V + sites[i];
+                        if (cand_margin) cand_margin[li] = margin_of_trace(m_trace(&Un));
+                        if (rejected) rejected[li] = 0;
+                        if (vp && label_of_trace(m_trace(&Un)) != ref_labels[li]) {
                             rej += 1;
+                            if (rejected) rejected[li] = 1;
                             continue;
                         }
                         link_put(&g, U, mu, sites[i], &Un);
@@ -472,8 +479,11 @@ int or_smooth(const int32_t dims[4], double *links, const int8_t *ref_labels, in
                 if (staple_sum(&g, old, mu, x, c0, c1, &S)) { err |= 1; continue; }
                 mat3 Ux = link_get(&g, old, mu, s);
                 mat3 Un = stout_candidate(&S, &Ux, rho[sw]);
+                if (cand_margin) cand_margin[i] = margin_of_trace(m_trace(&Un));
+                if (rejected) rejected[i] = 0;
                 if (vp && label_of_trace(m_trace(&Un)) != ref_labels[i]) {
                     rej += 1;
+                    if (rejected) rejected[i] = 1;
                     continue;
                 }
                 link_put(&g, U, mu, s, &Un);

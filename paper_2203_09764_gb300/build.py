@@ -12,11 +12,15 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+# VS_BUILD_DIR: build (and load) the library elsewhere, e.g. to compare variants
+OUT_DIR = os.environ.get("VS_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# VS_NVCC_EXTRA: extra nvcc flags, e.g. -DVS_SUBSWEEP_MINB=3 (blocks per SM of the
+# class-update kernel, which sets its register budget)
+FLAGS += os.environ.get("VS_NVCC_EXTRA", "").split()
 
 SOURCES = ["vs_sweep_f18.cu", "vs_sweep_f12.cu", "vs_sweep_d18.cu", "vs_kernels.cu",
            "vs_api.cu", "vs_serve.cu"]

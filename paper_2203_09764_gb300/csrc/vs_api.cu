@@ -40,6 +40,8 @@ extern "C" const char *vs_last_error(void) { return g_err; }
 
 extern "C" const char *vs_version(void) { return "vs 1.0 (sm_103a)"; }
 
+extern "C" int64_t vs_kernel_launches(void) { return (int64_t)launches(); }
+
 // ---------------------------------------------------------------------------
 // Context and device memory
 // ---------------------------------------------------------------------------
@@ -257,6 +259,7 @@ extern "C" vs_status vs_load_field(vs_field *f, const double *links, const int8_
     }
     if (where == VS_HOST) CK(cudaStreamSynchronize(f->stream));
     f->loaded = true;
+    f->sweeps_done = 0;
     return VS_OK;
 }
 
@@ -330,13 +333,14 @@ extern "C" vs_status vs_load_cooled(vs_field *f, uint64_t seed, int32_t n_cool) 
             for (int c = 0; c < 4; ++c) CK(launch_cool_class(p, f->nc, f->g, mu, c, f->U, f->stream));
     CK(launch_project(p, f->nc, f->g, f->U, f->ref, f->stream));
     f->loaded = true;
+    f->sweeps_done = 0;
     return VS_OK;
 }
 
 extern "C" vs_status vs_reunitarise(vs_field *f) {
     if (!f) return fail(VS_EINVAL, "vs_reunitarise: NULL field");
     CK(cudaSetDevice(f->ctx->opt.device));
-    CK(launch_reunit(f->prec == VS_FP32, f->nc, f->g, f->U, f->stream));
+    CK(launch_reunit(f->prec == VS_FP32, f->nc, f->g, f->U, nullptr, f->stream));
     return VS_OK;
 }
 
@@ -474,8 +478,8 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
             for (int mu = 0; mu < 4; ++mu) CK(subsweep_launch(f, rect, mu, p));
         }
         if (f->profiling) CK(cudaEventRecord(f->events[2 * s + 1], f->stream));
-        if (f->prec == VS_FP32 && a.reunit_every > 0 && (s + 1) % a.reunit_every == 0)
-            CK(launch_reunit(1, f->nc, f->g, f->U, f->stream));
+        if (f->prec == VS_FP32 && a.reunit_every > 0 && (f->sweeps_done + s + 1) % a.reunit_every == 0)
+            CK(launch_reunit(1, f->nc, f->g, f->U, vp ? f->ref : nullptr, f->stream));
         if (want_stats && a.action_every > 0 && (s + 1) % a.action_every == 0)
             CK(launch_action(f->prec == VS_FP32, f->nc, f->g, f->U, f->partials, f->sweep_actions + s, f->stream));
     }
@@ -489,6 +493,7 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
         }
     }
     f->last_action_every = a.action_every;
+    f->sweeps_done += n_sweeps;
     return VS_OK;
 }
 

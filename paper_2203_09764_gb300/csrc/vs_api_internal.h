@@ -48,6 +48,7 @@ struct vs_field {
     double *sweep_actions = nullptr;
     int sweep_cap = 0;
     int last_action_every = 0;
+    long long sweeps_done = 0;      // sweeps since the last load (re-unitarisation phase)
     bool profiling = false;
     double prof_ms = 0;
     int64_t prof_launches = 0;

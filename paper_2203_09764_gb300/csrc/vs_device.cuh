@@ -1,9 +1,10 @@
 // vs_device.cuh -- device-side SU(3) algebra, lattice geometry and field layout.
 //
-// Field layout in HBM (structure of arrays):
-//   links[mu][k][i]  T = float or double, k = 0..NC-1 real components
-//   (NC = 18: row-major 3x3 as re,im pairs; NC = 12: rows 0 and 1 only, row 2
-//   rebuilt as conj(row0 x row1) on load), i = site position in the plane.
+// Field layout in HBM (structure of vector planes):
+//   links of direction mu: NC reals per site (NC = 18: row-major 3x3 as
+//   re,im pairs; NC = 12: rows 0 and 1 only, row 2 rebuilt as
+//   conj(row0 x row1) on load), split into planes of float4 / float2 /
+//   double2 vectors (see load_link); i = site position in a plane.
 //   Site position: rows (y, z, t) in lexicographic order, and inside each
 //   x-row the sites grouped by x mod 4: i = row*Lx + (x & 3)*(Lx/4) + (x >> 2).
 //   For a colour class of the annealed schedule the updated sites of one
@@ -208,14 +209,33 @@ __device__ __forceinline__ void m3_scale(M3<T> &r, T s) {
 // Link load / store
 // --------------------------------------------------------------------------
 
+// Vector planes of one direction mu (element offset mu * NC * P):
+//   float, 18 reals : 4 planes of float4 (complex entries 0-1, 2-3, 4-5, 6-7)
+//                     then 1 plane of float2 (entry 8)
+//   float, 12 reals : 3 planes of float4 (entries 0-1, 2-3, 4-5); row 2 rebuilt
+//   double, 18 reals: 9 planes of double2 (one complex entry each)
+// A plane holding w reals per site starts at (reals before it) * P and site i
+// sits at w * i inside it, so every load is one aligned 8- or 16-byte vector.
 template <class T, int NC>
 __device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P, int mu, int i) {
-    const T *p = U + (long long)mu * NC * P + i;
+    const T *base = U + (long long)mu * NC * P;
     M3<T> m;
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int k = 0; k < NC / 2; ++k) {
-        m.re[k] = __ldg(p + (2 * k) * P);
-        m.im[k] = __ldg(p + (2 * k + 1) * P);
+        for (int q = 0; q < NC / 4; ++q) {
+            float4 v = __ldg(reinterpret_cast<const float4 *>(base + 4 * q * P) + i);
+            m.re[2 * q] = v.x; m.im[2 * q] = v.y; m.re[2 * q + 1] = v.z; m.im[2 * q + 1] = v.w;
+        }
+        if (NC == 18) {
+            float2 v = __ldg(reinterpret_cast<const float2 *>(base + 16 * P) + i);
+            m.re[8] = v.x; m.im[8] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < NC / 2; ++e) {
+            double2 v = __ldg(reinterpret_cast<const double2 *>(base + 2 * e * P) + i);
+            m.re[e] = v.x; m.im[e] = v.y;
+        }
     }
     if (NC == 12) {
         // row 2 = conj(row 0 x row 1)
@@ -235,11 +255,17 @@ __device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P,
 
 template <class T, int NC>
 __device__ __forceinline__ void store_link(T *__restrict__ U, long long P, int mu, int i, const M3<T> &m) {
-    T *p = U + (long long)mu * NC * P + i;
+    T *base = U + (long long)mu * NC * P;
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int k = 0; k < NC / 2; ++k) {
-        p[(2 * k) * P] = m.re[k];
-        p[(2 * k + 1) * P] = m.im[k];
+        for (int q = 0; q < NC / 4; ++q)
+            reinterpret_cast<float4 *>(base + 4 * q * P)[i] =
+                make_float4(m.re[2 * q], m.im[2 * q], m.re[2 * q + 1], m.im[2 * q + 1]);
+        if (NC == 18) reinterpret_cast<float2 *>(base + 16 * P)[i] = make_float2(m.re[8], m.im[8]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < NC / 2; ++e)
+            reinterpret_cast<double2 *>(base + 2 * e * P)[i] = make_double2(m.re[e], m.im[e]);
     }
 }
 

@@ -20,6 +20,10 @@ struct SubsweepParams {
     unsigned long long *counters;  // [0] rejects, [1] FP64 exponentials (may be null)
 };
 
+// process-wide count of direct kernel launches
+void count_launches(int n);
+long long launches();
+
 cudaError_t launch_subsweep_f18(bool rect, int mu, const SubsweepParams &p, cudaStream_t st);
 cudaError_t launch_subsweep_f12(bool rect, int mu, const SubsweepParams &p, cudaStream_t st);
 cudaError_t launch_subsweep_d18(bool rect, int mu, const SubsweepParams &p, cudaStream_t st);
@@ -45,7 +49,7 @@ cudaError_t launch_action(int prec, int nc, const Geo &g, const void *U, double 
 cudaError_t launch_vortex(int prec, int nc, const Geo &g, const void *U, const int8_t *ref,
                           int8_t *cur, unsigned long long *counts,
                           unsigned long long *margin_bits, cudaStream_t st);
-cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, cudaStream_t st);
+cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, const int8_t *ref, cudaStream_t st);
 cudaError_t launch_debug_expm(int prec, const double *X, int n, double *E, cudaStream_t st);
 cudaError_t launch_haar(int prec, int nc, const Geo &g, uint64_t seed, void *U, cudaStream_t st);
 cudaError_t launch_cool_class(int prec, int nc, const Geo &g, int mu, int colour, void *U,

@@ -1,5 +1,6 @@
 // vs_kernels.cu -- load/read conversions, centrifuge, action, vortex check,
 // re-unitarisation, hot-start generation and the exponential diagnostic.
+#include <atomic>
 #include <cmath>
 
 #include "vs_internal.h"
@@ -252,8 +253,11 @@ __global__ void k_vortex_charges(Geo g, const int8_t *__restrict__ ref, const in
 // r2 = conj(r0 x r1).
 // ---------------------------------------------------------------------------
 
+// With ref != nullptr (vortex preservation on) a re-unitarised link whose
+// Z(3) label would differ from the reference is left as it was, so every
+// stored link keeps its original label.
 template <class T, int NC>
-__global__ void k_reunit(Geo g, T *U) {
+__global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= 4ll * g.V) return;
     int mu = (int)(l / g.V), i = (int)(l % g.V);
@@ -287,6 +291,9 @@ __global__ void k_reunit(Geo g, T *U) {
     }
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) { m.re[3 * a + b] = T(r[a][b]); m.im[3 * a + b] = T(im[a][b]); }
+    if (ref && z3_label<T>(m.re[0] + m.re[4] + m.re[8], m.im[0] + m.im[4] + m.im[8]) !=
+                   (int)ref[(long long)mu * g.P + i])
+        return;
     store_link<T, NC>(U, g.P, mu, i, m);
 }
 
@@ -444,6 +451,10 @@ __global__ void k_project(Geo g, T *U, int8_t *ref) {
 // Dispatch
 // ---------------------------------------------------------------------------
 
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
 #define VS_DISPATCH(prec, nc, KERNEL, ...)                                          \
     do {                                                                            \
         if ((prec) == 0 && (nc) == 18) { KERNEL<double, 18>__VA_ARGS__; }           \
@@ -458,6 +469,7 @@ cudaError_t launch_load_labels(int prec, int nc, const Geo &g, const int8_t *lab
     if (prec == 0) k_load_labels<double, 18><<<b, kThreads, 0, st>>>(g, lab, (double *)U, ref);
     else if (nc == 18) k_load_labels<float, 18><<<b, kThreads, 0, st>>>(g, lab, (float *)U, ref);
     else k_load_labels<float, 12><<<b, kThreads, 0, st>>>(g, lab, (float *)U, ref);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -467,6 +479,7 @@ cudaError_t launch_load_links(int prec, int nc, const Geo &g, const double *in, 
     if (prec == 0) k_load_links<double, 18><<<b, kThreads, 0, st>>>(g, in, (double *)U, ref);
     else if (nc == 18) k_load_links<float, 18><<<b, kThreads, 0, st>>>(g, in, (float *)U, ref);
     else k_load_links<float, 12><<<b, kThreads, 0, st>>>(g, in, (float *)U, ref);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -475,11 +488,13 @@ cudaError_t launch_read_links(int prec, int nc, const Geo &g, const void *U, dou
     if (prec == 0) k_read_links<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, out);
     else if (nc == 18) k_read_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
     else k_read_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_read_labels(const Geo &g, const int8_t *ref, int8_t *out, cudaStream_t st) {
     k_read_labels<<<nblocks(4ll * g.V), kThreads, 0, st>>>(g, ref, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -488,6 +503,7 @@ cudaError_t launch_current_labels(int prec, int nc, const Geo &g, const void *U,
     if (prec == 0) k_current_labels<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, out);
     else if (nc == 18) k_current_labels<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
     else k_current_labels<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -497,6 +513,7 @@ cudaError_t launch_centrifuge(int prec, int nc, const Geo &g, const int8_t *ref,
     if (prec == 0) k_centrifuge<double, 18><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (double *)U);
     else if (nc == 18) k_centrifuge<float, 18><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (float *)U);
     else k_centrifuge<float, 12><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (float *)U);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -513,6 +530,7 @@ cudaError_t launch_action(int prec, int nc, const Geo &g, const void *U, double 
     else k_action<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, partials);
     // <S>/beta = (1/V) sum_x (2/72) sum_{mu<nu} (3 - Re Tr P)
     k_sum_partials<<<1, 1024, 0, st>>>(partials, b, 2.0 / 72.0 / (double)g.V, out);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -523,20 +541,23 @@ cudaError_t launch_vortex(int prec, int nc, const Geo &g, const void *U, const i
     else if (nc == 18) k_vortex_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits);
     else k_vortex_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits);
     k_vortex_charges<<<nblocks(g.V), kThreads, 0, st>>>(g, ref, cur, counts);
+    count_launches(2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, cudaStream_t st) {
+cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, const int8_t *ref, cudaStream_t st) {
     int b = nblocks(4ll * g.V);
-    if (prec == 0) k_reunit<double, 18><<<b, kThreads, 0, st>>>(g, (double *)U);
-    else if (nc == 18) k_reunit<float, 18><<<b, kThreads, 0, st>>>(g, (float *)U);
-    else k_reunit<float, 12><<<b, kThreads, 0, st>>>(g, (float *)U);
+    if (prec == 0) k_reunit<double, 18><<<b, kThreads, 0, st>>>(g, (double *)U, ref);
+    else if (nc == 18) k_reunit<float, 18><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
+    else k_reunit<float, 12><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_debug_expm(int prec, const double *X, int n, double *E, cudaStream_t st) {
     if (prec == 0) k_debug_expm<double><<<nblocks(n), kThreads, 0, st>>>(X, n, E);
     else k_debug_expm<float><<<nblocks(n), kThreads, 0, st>>>(X, n, E);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -545,6 +566,7 @@ cudaError_t launch_haar(int prec, int nc, const Geo &g, uint64_t seed, void *U, 
     if (prec == 0) k_haar<double, 18><<<b, kThreads, 0, st>>>(g, seed, (double *)U);
     else if (nc == 18) k_haar<float, 18><<<b, kThreads, 0, st>>>(g, seed, (float *)U);
     else k_haar<float, 12><<<b, kThreads, 0, st>>>(g, seed, (float *)U);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -557,6 +579,7 @@ static cudaError_t cool_tpl(const Geo &g, int mu, int colour, T *U, cudaStream_t
         case 2: k_cool<T, NC, 2><<<b, 128, 0, st>>>(g, colour, U); break;
         default: k_cool<T, NC, 3><<<b, 128, 0, st>>>(g, colour, U); break;
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -571,6 +594,7 @@ cudaError_t launch_project(int prec, int nc, const Geo &g, void *U, int8_t *ref,
     if (prec == 0) k_project<double, 18><<<b, kThreads, 0, st>>>(g, (double *)U, ref);
     else if (nc == 18) k_project<float, 18><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
     else k_project<float, 12><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
+    count_launches(1);
     return cudaGetLastError();
 }
 

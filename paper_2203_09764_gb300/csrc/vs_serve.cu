@@ -172,6 +172,7 @@ static vs_status enqueue_chunk(Job &j, unsigned long long *ctr) {
     if (n == j.chunk && (s.reunit_every <= 0 || j.chunk % s.reunit_every == 0)) {
         if (!j.graph) {
             cudaGraph_t g = nullptr;
+            f->sweeps_done = 0;      // the captured chunk starts a re-unitarisation period
             if (cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return fail(VS_EDEVICE, "stream capture failed");
             vs_status st = smooth_enqueue(f, n, s.rho, s.epsilon, s.u0, &a, s.vortex_preserve, false, ctr);
@@ -188,7 +189,9 @@ static vs_status enqueue_chunk(Job &j, unsigned long long *ctr) {
         cudaError_t e = cudaGraphLaunch(j.graph, f->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     } else {
-        // final partial chunk: reunitarisation phase continues from the sweep count
+        // final partial chunk: graph replays do not advance the host-side sweep
+        // count, so set the re-unitarisation phase from the sweeps enqueued
+        f->sweeps_done = j.sweeps_enqueued;
         vs_status st = smooth_enqueue(f, n, s.rho, s.epsilon, s.u0, &a, s.vortex_preserve, false, ctr);
         if (st != VS_OK) return st;
     }

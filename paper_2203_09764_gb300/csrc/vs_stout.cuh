@@ -41,60 +41,91 @@ __device__ __forceinline__ M3<T> path_step(const Geo &g, const T *__restrict__ U
     return m3_dag(load_link<T, NC>(U, g.P, d, sidx(g, mv(g, p, d, -1))));
 }
 
-// Sigma_mu(x) for link (x, MU) read from field U.
+// Sigma_mu(x) for link (x, MU) read from field U, in three passes over the six
+// directions (nu, s) so that only one accumulator is live at a time:
+//   1. wide forward  F  = sum A B U_mu(x+s nu+mu) (step -s nu from x+s nu+2mu),
+//                    Sigma  = c1 F U_mu^dag(x+mu)
+//   2. wide backward Bk = sum (step s nu from x-mu) U_mu(x-mu+s nu) B C,
+//                    Sigma += c1 U_mu^dag(x-mu) Bk
+//   3. staples + tall rectangles: Sigma += A (c0 B + c1 T) C
+// with A = step s nu from x, B = U_mu(x+s nu), C = step -s nu from x+s nu+mu
+// and T = (step s nu from x+s nu) U_mu(x+2s nu) (step -s nu from x+2s nu+mu).
+// 10 products per direction plus 2.  Without rectangles: Sigma = c0 sum A B C.
 template <class T, int NC, bool RECT, int MU>
 __device__ __forceinline__ M3<T> staple_sum(const Geo &g, const T *__restrict__ U, Pt x, T c0, T c1) {
-    M3<T> sig, F, Bk;
-    m3_zero(sig);
-    if (RECT) { m3_zero(F); m3_zero(Bk); }
+    M3<T> sig;
+    if (RECT) {
+        {
+            M3<T> F;
+            m3_zero(F);
+#pragma unroll 1
+            for (int j = 1; j < 4; ++j) {
+                const int nu = (MU + j) & 3;
 #pragma unroll
-    for (int j = 1; j < 4; ++j) {
-        const int nu = (MU + j) & 3;
+                for (int s = 1; s >= -1; s -= 2) {
+                    Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1);
+                    M3<T> W = m3_mul(path_step<T, NC>(g, U, x, nu, s),
+                                     load_link<T, NC>(U, g.P, MU, sidx(g, xs)));
+                    W = m3_mul(W, load_link<T, NC>(U, g.P, MU, sidx(g, xsm)));
+                    m3_madd(F, W, path_step<T, NC>(g, U, mv(g, xsm, MU, 1), nu, -s));
+                }
+            }
+            sig = m3_mul_nd(F, load_link<T, NC>(U, g.P, MU, sidx(g, mv(g, x, MU, 1))));
+            m3_scale(sig, c1);
+        }
+        {
+            M3<T> Bk;
+            m3_zero(Bk);
+            const Pt xm = mv(g, x, MU, -1);
+#pragma unroll 1
+            for (int j = 1; j < 4; ++j) {
+                const int nu = (MU + j) & 3;
 #pragma unroll
-        for (int s = 1; s >= -1; s -= 2) {
-            Pt xs = mv(g, x, nu, s);                        // x + s nu
-            Pt xsm = mv(g, xs, MU, 1);                      // x + s nu + mu
-            M3<T> A = path_step<T, NC>(g, U, x, nu, s);
-            M3<T> B = load_link<T, NC>(U, g.P, MU, sidx(g, xs));
-            M3<T> C = path_step<T, NC>(g, U, xsm, nu, -s);
-            M3<T> AB = m3_mul(A, B);
-            if (!RECT) {
-                m3_madd(sig, AB, C);
-            } else {
-                // tall: A (step s nu from xs) U_mu(x + 2 s nu) (step -s nu from x + 2s nu + mu) C
-                Pt x2s = mv(g, xs, nu, s);
-                M3<T> T1 = m3_mul(path_step<T, NC>(g, U, xs, nu, s),
+                for (int s = 1; s >= -1; s -= 2) {
+                    Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1);
+                    M3<T> BC = m3_mul(load_link<T, NC>(U, g.P, MU, sidx(g, xs)),
+                                      path_step<T, NC>(g, U, xsm, nu, -s));
+                    M3<T> Y = m3_mul(path_step<T, NC>(g, U, xm, nu, s),
+                                     load_link<T, NC>(U, g.P, MU, sidx(g, mv(g, xm, nu, s))));
+                    m3_madd(Bk, Y, BC);
+                }
+            }
+            M3<T> t = m3_mul_dn(load_link<T, NC>(U, g.P, MU, sidx(g, xm)), Bk);
+            m3_axpy(sig, c1, t);
+        }
+#pragma unroll 1
+        for (int j = 1; j < 4; ++j) {
+            const int nu = (MU + j) & 3;
+#pragma unroll
+            for (int s = 1; s >= -1; s -= 2) {
+                Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1), x2s = mv(g, xs, nu, s);
+                M3<T> Tt = m3_mul(path_step<T, NC>(g, U, xs, nu, s),
                                   load_link<T, NC>(U, g.P, MU, sidx(g, x2s)));
-                M3<T> Tt = m3_mul(T1, path_step<T, NC>(g, U, mv(g, x2s, MU, 1), nu, -s));
-                M3<T> M = m3_mul(A, Tt);
-                m3_scale(M, c1);
-                m3_axpy(M, c0, AB);
-                m3_madd(sig, M, C);
-                // wide forward (without the final U_mu^dag(x + mu)):
-                //   A B U_mu(x + s nu + mu) (step -s nu from x + s nu + 2 mu)
-                M3<T> W = m3_mul(AB, load_link<T, NC>(U, g.P, MU, sidx(g, xsm)));
-                m3_madd(F, W, path_step<T, NC>(g, U, mv(g, xsm, MU, 1), nu, -s));
-                // wide backward (without the leading U_mu^dag(x - mu)):
-                //   (step s nu from x - mu) U_mu(x - mu + s nu) B C
-                Pt xm = mv(g, x, MU, -1);
-                M3<T> Y = m3_mul(path_step<T, NC>(g, U, xm, nu, s),
-                                 load_link<T, NC>(U, g.P, MU, sidx(g, mv(g, xm, nu, s))));
-                m3_madd(Bk, Y, m3_mul(B, C));
+                Tt = m3_mul(Tt, path_step<T, NC>(g, U, mv(g, x2s, MU, 1), nu, -s));
+                M3<T> N = load_link<T, NC>(U, g.P, MU, sidx(g, xs));
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    N.re[k] = fma(c1, Tt.re[k], c0 * N.re[k]);
+                    N.im[k] = fma(c1, Tt.im[k], c0 * N.im[k]);
+                }
+                M3<T> AN = m3_mul(path_step<T, NC>(g, U, x, nu, s), N);
+                m3_madd(sig, AN, path_step<T, NC>(g, U, xsm, nu, -s));
             }
         }
-    }
-    if (!RECT) {
-        if (c0 != T(1)) m3_scale(sig, c0);
     } else {
-        M3<T> up = load_link<T, NC>(U, g.P, MU, sidx(g, mv(g, x, MU, 1)));
-        M3<T> um = load_link<T, NC>(U, g.P, MU, sidx(g, mv(g, x, MU, -1)));
-        M3<T> t1 = m3_mul_nd(F, up);
-        M3<T> t2 = m3_mul_dn(um, Bk);
+        m3_zero(sig);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            sig.re[k] = fma(c1, t1.re[k] + t2.re[k], sig.re[k]);
-            sig.im[k] = fma(c1, t1.im[k] + t2.im[k], sig.im[k]);
+        for (int j = 1; j < 4; ++j) {
+            const int nu = (MU + j) & 3;
+#pragma unroll
+            for (int s = 1; s >= -1; s -= 2) {
+                Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1);
+                M3<T> AB = m3_mul(path_step<T, NC>(g, U, x, nu, s),
+                                  load_link<T, NC>(U, g.P, MU, sidx(g, xs)));
+                m3_madd(sig, AB, path_step<T, NC>(g, U, xsm, nu, -s));
+            }
         }
+        if (c0 != T(1)) m3_scale(sig, c0);
     }
     return sig;
 }
@@ -204,8 +235,15 @@ __device__ __forceinline__ M3<T> stout_candidate(const M3<T> &sig, const M3<T> &
     return m3_mul(Mx, Ux);
 }
 
+#ifndef VS_SUBSWEEP_MINB
+#define VS_SUBSWEEP_MINB 4
+#endif
+
+// One thread per link of the colour class (or of direction MU when colour < 0).
+// FP32: at most 65536 / (128 * VS_SUBSWEEP_MINB) registers per thread, so
+// VS_SUBSWEEP_MINB blocks of 128 threads fit on an SM.
 template <class T, int NC, bool RECT, int MU>
-__global__ void __launch_bounds__(128) k_subsweep(SubsweepParams a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1) k_subsweep(SubsweepParams a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
     bool reject = false, used64 = false;

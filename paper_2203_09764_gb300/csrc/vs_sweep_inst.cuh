@@ -30,6 +30,7 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
         }
     }
 #undef VS_LAUNCH
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -124,6 +124,7 @@ _SIGS = {
     "vs_cancel": (ctypes.c_int32, [P, ctypes.c_int64]),
     "vs_serve_stats_get": (ctypes.c_int32, [P, ctypes.POINTER(vs_serve_stats)]),
     "vs_now_ms": (ctypes.c_double, [P]),
+    "vs_kernel_launches": (ctypes.c_int64, []),
 }
 
 
@@ -166,12 +167,17 @@ def _dims(dims):
     return (ctypes.c_int32 * 4)(*[int(d) for d in dims])
 
 
+_CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the default stream, distinct from NULL
+
+
 def _stream(s):
+    """None -> NULL (the library creates a stream); a torch stream or handle ->
+    that stream, with torch's default stream (handle 0) passed as
+    cudaStreamLegacy so that work stays ordered with torch's own work."""
     if s is None:
         return None
-    if hasattr(s, "cuda_stream"):
-        return ctypes.c_void_p(s.cuda_stream)
-    return ctypes.c_void_p(int(s))
+    h = s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+    return ctypes.c_void_p(h if h else _CUDA_STREAM_LEGACY)
 
 
 # ---------------------------------------------------------------------------
@@ -441,3 +447,7 @@ def vs_serve_stats_get(ctx):
 
 def vs_now_ms(ctx):
     return float(lib.vs_now_ms(ctx))
+
+
+def vs_kernel_launches():
+    return int(lib.vs_kernel_launches())

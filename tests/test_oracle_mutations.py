@@ -60,7 +60,7 @@ MUTATIONS = [
      "const pstep plaq[4] = {{mu, +1}, {nu, +1}, {nu, -1}, {mu, -1}};",
      pins.test_action_closed_forms, ()),
     ("vortex preservation against the current label",
-     "if (vp && label_of_trace(m_trace(&Un)) != ref_labels[(long)mu * g.V + sites[i]]) {",
+     "if (vp && label_of_trace(m_trace(&Un)) != ref_labels[li]) {",
      "if (vp && label_of_trace(m_trace(&Un)) != label_of_trace(m_trace(&Ux))) {",
      pins.test_vortex_preservation_keeps_original_labels, ()),
     ("cooling subgroup conjugation",
