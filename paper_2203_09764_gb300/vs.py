@@ -125,7 +125,11 @@ _SIGS = {
     "vs_serve_stats_get": (ctypes.c_int32, [P, ctypes.POINTER(vs_serve_stats)]),
     "vs_now_ms": (ctypes.c_double, [P]),
     "vs_kernel_launches": (ctypes.c_int64, []),
+    "vs_vortex_check_noalloc": (ctypes.c_int32, [P, P, P, ctypes.c_int32, ctypes.c_int32, P,
+                                                 ctypes.POINTER(vs_vortex_report)]),
 }
+
+VS_NOALLOC_MAX_LINKS = 8 * 1024 * 1024
 
 
 def _load():
@@ -301,6 +305,17 @@ def vs_subsweep(f, mu, colour, rho, epsilon=1.0, u0=1.0, vortex_preserve=True):
 def vs_vortex_check(f):
     r = vs_vortex_report()
     _check(lib.vs_vortex_check(f, ctypes.byref(r)))
+    return dict(n_links=r.n_links, n_label_diff=r.n_label_diff, n_charge_diff=r.n_charge_diff,
+                n_near_boundary=r.n_near_boundary, min_margin=r.min_margin)
+
+
+def vs_vortex_check_noalloc(links, ref_labels, dims, precision, storage, stream=None):
+    """The vortex check on caller-owned device buffers (device pointers as
+    integers, e.g. from vs_field_describe), with no allocation; see vs.h."""
+    r = vs_vortex_report()
+    _check(lib.vs_vortex_check_noalloc(ctypes.c_void_p(int(links)), ctypes.c_void_p(int(ref_labels)),
+                                       _dims(dims), int(precision), int(storage), _stream(stream),
+                                       ctypes.byref(r)))
     return dict(n_links=r.n_links, n_label_diff=r.n_label_diff, n_charge_diff=r.n_charge_diff,
                 n_near_boundary=r.n_near_boundary, min_margin=r.min_margin)
 

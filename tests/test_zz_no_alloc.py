@@ -1,0 +1,59 @@
+"""vs_vortex_check_noalloc: the vortex check for callers that cannot allocate.
+
+Through the C ABI, its reports must equal those of vs_vortex_check (integer
+counts exactly, the minimum margin exactly: same kernels, same inputs) on two
+calls in a row, so that the shared scratch array carries nothing over from one
+call to the next.  Kept in its own file so pytest collects it last.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+vs = pytest.importorskip("paper_2203_09764_gb300.vs")
+
+
+def _smoothed_field(ctx, dims, precision, storage):
+    f = vs.vs_field_create(ctx, dims, precision, storage)
+    vs.vs_load_cooled(f, 7, 3)
+    vs.vs_centrifuge(f, 0.02, 1234)
+    # without vortex preservation and with large steps some labels move, so
+    # the counts under test are not all zero
+    vs.vs_smooth(f, 3, 0.3, -0.25, vortex_preserve=False)
+    vs.vs_synchronize(f)
+    return f
+
+
+@pytest.mark.parametrize("precision,storage,dims", [
+    (vs.VS_FP32, vs.VS_LINK18, (16, 16, 16, 32)),
+    (vs.VS_FP64, vs.VS_LINK18, (8, 8, 8, 16)),
+    (vs.VS_FP32, vs.VS_LINK12, (8, 8, 12, 16)),
+])
+def test_noalloc_matches_field_check_on_two_calls(precision, storage, dims):
+    ctx = vs.vs_create(0)
+    try:
+        f = _smoothed_field(ctx, dims, precision, storage)
+        ref = vs.vs_vortex_check(f)
+        assert ref["n_label_diff"] > 0 and ref["n_charge_diff"] > 0
+        d = vs.vs_field_describe(f)
+        got = [vs.vs_vortex_check_noalloc(d["links"], d["labels"], dims, precision, storage,
+                                          d["stream"]) for _ in range(2)]
+        vs.vs_field_destroy(f)
+    finally:
+        vs.vs_destroy(ctx)
+    for g in got:
+        assert g["n_links"] == ref["n_links"]
+        assert g["n_label_diff"] == ref["n_label_diff"]
+        assert g["n_charge_diff"] == ref["n_charge_diff"]
+        assert g["n_near_boundary"] == ref["n_near_boundary"]
+        assert g["min_margin"] == ref["min_margin"]
+
+
+def test_noalloc_rejects_lattices_beyond_its_scratch():
+    dims = (32, 32, 32, 128)          # 4 V = 2^24 links > VS_NOALLOC_MAX_LINKS
+    with pytest.raises(vs.VSError) as ei:
+        vs.vs_vortex_check_noalloc(1, 1, dims, vs.VS_FP32, vs.VS_LINK18)
+    assert ei.value.status == vs.VS_EINVAL
+    assert "scratch" in str(ei.value)
+    assert 4 * 32 * 32 * 32 * 64 <= vs.VS_NOALLOC_MAX_LINKS
