@@ -400,6 +400,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_scaling(args):
+    """Lattice-size sweep (16^3x32 .. 48^3x96): link-updates/s and the roofline
+    fraction of the class-update kernel per size, FP32 18- and 12-real; one
+    JSON line per size."""
+    import torch
+    from paper_2203_09764_gb300 import vs
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = vs.vs_create(0)
+    peaks, src = _measured_peaks()
+    for dims in [(16, 16, 16, 32), (24, 24, 24, 48), (32, 32, 32, 64), (40, 40, 40, 80), (48, 48, 48, 96)]:
+        for storage, nc in ((vs.VS_LINK18, 18), (vs.VS_LINK12, 12)):
+            V = int(np.prod(dims))
+            f = vs.vs_field_create(ctx, dims, vs.VS_FP32, storage, stream)
+            vs.vs_load_cooled(f, 5, N_COOL)
+            vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+            vs.vs_smooth(f, 3, RHO, EPS, U0, reunit_every=REUNIT)
+            vs.vs_synchronize(f)
+            vs.vs_set_profiling(f, True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vs.vs_smooth(f, args.sweeps, RHO, EPS, U0, reunit_every=REUNIT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            cms, nl = vs.vs_get_profile(f)
+            vs.vs_field_destroy(f)
+            per = cms / nl
+            bpu = BYTES_PER_UPDATE[(1, nc)]
+            ach = V / 4 * bpu / (per / 1e3) / 1e9
+            print(json.dumps({"lattice": list(dims), "storage": "%d-real" % nc, "sweeps": args.sweeps,
+                              "link_updates_per_s": 4 * V * args.sweeps / (ms / 1e3),
+                              "class_launch_ms": per, "achieved_gbs": ach,
+                              "hbm_frac": ach / peaks["hbm_gbs"], "peak_source": src,
+                              "field_mb": 4 * nc * 4 * V / 1e6}), flush=True)
+    vs.vs_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,11 +454,17 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scaling", action="store_true",
+                    help="lattice-size sweep 16^3x32 .. 48^3x96 instead of the benchmark step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.scaling:
+        if args.sweeps == N_SWEEPS:
+            args.sweeps = 20
+        run_scaling(args)
     else:
         run_ours(args)
 

@@ -249,48 +249,57 @@ __global__ void k_vortex_charges(Geo g, const int8_t *__restrict__ ref, const in
 }
 
 // ---------------------------------------------------------------------------
-// Re-unitarisation in FP64: r0 /= |r0|; r1 -= (r0^dag r1) r0; r1 /= |r1|;
-// r2 = conj(r0 x r1).
-// ---------------------------------------------------------------------------
-
+// Re-unitarisation: r0 /= |r0|; r1 -= (r0^dag r1) r0; r1 /= |r1|;
+// r2 = conj(r0 x r1).  The norms and the inner product are accumulated in
+// FP64 (the part that decides how unitary the result is); the vector updates
+// run in the storage precision.
 // With ref != nullptr (vortex preservation on) a re-unitarised link whose
 // Z(3) label would differ from the reference is left as it was, so every
 // stored link keeps its original label.
+// ---------------------------------------------------------------------------
+
 template <class T, int NC>
 __global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= 4ll * g.V) return;
     int mu = (int)(l / g.V), i = (int)(l % g.V);
     M3<T> m = load_link<T, NC>(U, g.P, mu, i);
-    double r[3][3], im[3][3];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 3; ++b) { r[a][b] = m.re[3 * a + b]; im[a][b] = m.im[3 * a + b]; }
     double n0 = 0;
-    for (int b = 0; b < 3; ++b) n0 += r[0][b] * r[0][b] + im[0][b] * im[0][b];
-    n0 = 1.0 / sqrt(n0);
-    for (int b = 0; b < 3; ++b) { r[0][b] *= n0; im[0][b] *= n0; }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        n0 = fma((double)m.re[b], (double)m.re[b], fma((double)m.im[b], (double)m.im[b], n0));
+    const T s0 = T(1.0 / sqrt(n0));
+#pragma unroll
+    for (int b = 0; b < 3; ++b) { m.re[b] *= s0; m.im[b] *= s0; }
     double pr = 0, pi = 0;  // r0^dag r1
+#pragma unroll
     for (int b = 0; b < 3; ++b) {
-        pr += r[0][b] * r[1][b] + im[0][b] * im[1][b];
-        pi += r[0][b] * im[1][b] - im[0][b] * r[1][b];
+        pr = fma((double)m.re[b], (double)m.re[3 + b], fma((double)m.im[b], (double)m.im[3 + b], pr));
+        pi = fma((double)m.re[b], (double)m.im[3 + b], fma(-(double)m.im[b], (double)m.re[3 + b], pi));
     }
+    const T tpr = T(pr), tpi = T(pi);
+#pragma unroll
     for (int b = 0; b < 3; ++b) {
-        r[1][b] -= pr * r[0][b] - pi * im[0][b];
-        im[1][b] -= pr * im[0][b] + pi * r[0][b];
+        T r1 = m.re[3 + b] - (tpr * m.re[b] - tpi * m.im[b]);
+        T i1 = m.im[3 + b] - (tpr * m.im[b] + tpi * m.re[b]);
+        m.re[3 + b] = r1;
+        m.im[3 + b] = i1;
     }
     double n1 = 0;
-    for (int b = 0; b < 3; ++b) n1 += r[1][b] * r[1][b] + im[1][b] * im[1][b];
-    n1 = 1.0 / sqrt(n1);
-    for (int b = 0; b < 3; ++b) { r[1][b] *= n1; im[1][b] *= n1; }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        n1 = fma((double)m.re[3 + b], (double)m.re[3 + b], fma((double)m.im[3 + b], (double)m.im[3 + b], n1));
+    const T s1 = T(1.0 / sqrt(n1));
+#pragma unroll
+    for (int b = 0; b < 3; ++b) { m.re[3 + b] *= s1; m.im[3 + b] *= s1; }
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
-        int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-        double cr = r[0][j1] * r[1][j2] - im[0][j1] * im[1][j2] - (r[0][j2] * r[1][j1] - im[0][j2] * im[1][j1]);
-        double ci = r[0][j1] * im[1][j2] + im[0][j1] * r[1][j2] - (r[0][j2] * im[1][j1] + im[0][j2] * r[1][j1]);
-        r[2][j] = cr;
-        im[2][j] = -ci;
+        const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        T cr = m.re[j1] * m.re[3 + j2] - m.im[j1] * m.im[3 + j2] - (m.re[j2] * m.re[3 + j1] - m.im[j2] * m.im[3 + j1]);
+        T ci = m.re[j1] * m.im[3 + j2] + m.im[j1] * m.re[3 + j2] - (m.re[j2] * m.im[3 + j1] + m.im[j2] * m.re[3 + j1]);
+        m.re[6 + j] = cr;
+        m.im[6 + j] = -ci;
     }
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) { m.re[3 * a + b] = T(r[a][b]); m.im[3 * a + b] = T(im[a][b]); }
     if (ref && z3_label<T>(m.re[0] + m.re[4] + m.re[8], m.im[0] + m.im[4] + m.im[8]) !=
                    (int)ref[(long long)mu * g.P + i])
         return;

@@ -34,11 +34,28 @@ template <class T> struct Tol;
 template <> struct Tol<float> { static __device__ __forceinline__ float eps() { return 1.5e-8f; } };
 template <> struct Tol<double> { static __device__ __forceinline__ double eps() { return 1e-17; } };
 
-// Step of a lattice path from site p: s > 0 -> U_d(p); s < 0 -> U_d(p - d)^dag.
+// The plane position is a sum of one term per coordinate,
+//   i(x) = Xpos(x0) + Lx x1 + Lx Ly x2 + Lx Ly Lz x3,  Xpos(x0) = (x0 & 3) Lx/4 + x0/4,
+// so the position of x + a e_nu + b e_mu is i(x) + D_nu(a) + D_mu(b) with
+// D_d(a) = i(x + a e_d) - i(x) for the periodic shift along d alone.
+__device__ __forceinline__ int shift_delta(const Geo &g, const Pt &x, int d, int a) {
+    if (d == 0) {
+        const int xn = wrapc(x.x0 + a, g.L[0]);
+        return ((xn & 3) - (x.x0 & 3)) * g.Q + ((xn >> 2) - (x.x0 >> 2));
+    }
+    // explicit selects: indexing the kernel-parameter array with a runtime d
+    // would force a copy of the parameters to local memory
+    const int xd = d == 1 ? x.x1 : (d == 2 ? x.x2 : x.x3);
+    const int Ld = d == 1 ? g.L[1] : (d == 2 ? g.L[2] : g.L[3]);
+    const int st = d == 1 ? g.L[0] : (d == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2]);
+    return (wrapc(xd + a, Ld) - xd) * st;
+}
+
+// Link of direction d at plane position i, daggered when dag is true.
 template <class T, int NC>
-__device__ __forceinline__ M3<T> path_step(const Geo &g, const T *__restrict__ U, Pt p, int d, int s) {
-    if (s > 0) return load_link<T, NC>(U, g.P, d, sidx(g, p));
-    return m3_dag(load_link<T, NC>(U, g.P, d, sidx(g, mv(g, p, d, -1))));
+__device__ __forceinline__ M3<T> link_at(const Geo &g, const T *__restrict__ U, int d, int i, bool dag) {
+    M3<T> m = load_link<T, NC>(U, g.P, d, i);
+    return dag ? m3_dag(m) : m;
 }
 
 // Sigma_mu(x) for link (x, MU) read from field U, in three passes over the six
@@ -51,78 +68,120 @@ __device__ __forceinline__ M3<T> path_step(const Geo &g, const T *__restrict__ U
 // with A = step s nu from x, B = U_mu(x+s nu), C = step -s nu from x+s nu+mu
 // and T = (step s nu from x+s nu) U_mu(x+2s nu) (step -s nu from x+2s nu+mu).
 // 10 products per direction plus 2.  Without rectangles: Sigma = c0 sum A B C.
+// A path step from site p along +nu is U_nu(p); along -nu it is U_nu(p - nu)^dag.
+// Sites are written x + a nu + b mu and addressed as i0 + Dn(a) + Dm(b).
+// Plane positions around one link: i0 and the shifts along mu (b = -1, 1, 2)
+// and along the current nu (a = -2, -1, 1, 2).
+struct Around {
+    int i0, dmm1, dmp1, dmp2, dnm2, dnm1, dnp1, dnp2;
+};
+
+__device__ __forceinline__ int around_pos(const Around &S, int a, int b) {
+    const int da = a == 0 ? 0 : (a == -1 ? S.dnm1 : (a == 1 ? S.dnp1 : (a == -2 ? S.dnm2 : S.dnp2)));
+    const int db = b == 0 ? 0 : (b == -1 ? S.dmm1 : (b == 1 ? S.dmp1 : S.dmp2));
+    return S.i0 + da + db;
+}
+
+__device__ __forceinline__ void around_nu(const Geo &g, const Pt &x, int nu, bool rect, Around &S) {
+    S.dnm1 = shift_delta(g, x, nu, -1);
+    S.dnp1 = shift_delta(g, x, nu, 1);
+    S.dnm2 = rect ? shift_delta(g, x, nu, -2) : 0;
+    S.dnp2 = rect ? shift_delta(g, x, nu, 2) : 0;
+}
+
+// Path step along s*nu from site x + a nu + b mu.
+template <class T, int NC>
+__device__ __forceinline__ M3<T> step_fwd(const Geo &g, const T *__restrict__ U, const Around &S, int nu,
+                                          int s, int a, int b) {
+    return s > 0 ? link_at<T, NC>(g, U, nu, around_pos(S, a, b), false)
+                 : link_at<T, NC>(g, U, nu, around_pos(S, a - 1, b), true);
+}
+
+// Path step along -s*nu from site x + a nu + b mu.
+template <class T, int NC>
+__device__ __forceinline__ M3<T> step_back(const Geo &g, const T *__restrict__ U, const Around &S, int nu,
+                                           int s, int a, int b) {
+    return s > 0 ? link_at<T, NC>(g, U, nu, around_pos(S, a - 1, b), true)
+                 : link_at<T, NC>(g, U, nu, around_pos(S, a, b), false);
+}
+
+template <class T, int NC, int MU>
+__device__ __forceinline__ M3<T> link_mu(const Geo &g, const T *__restrict__ U, const Around &S, int a, int b) {
+    return link_at<T, NC>(g, U, MU, around_pos(S, a, b), false);
+}
+
 template <class T, int NC, bool RECT, int MU>
 __device__ __forceinline__ M3<T> staple_sum(const Geo &g, const T *__restrict__ U, Pt x, T c0, T c1) {
+    Around S;
+    S.i0 = sidx(g, x);
+    S.dmm1 = shift_delta(g, x, MU, -1);
+    S.dmp1 = shift_delta(g, x, MU, 1);
+    S.dmp2 = RECT ? shift_delta(g, x, MU, 2) : 0;
     M3<T> sig;
+    m3_zero(sig);
     if (RECT) {
-        {
+        {   // 1. wide forward: F = sum A B U_mu(s,1) back(s,2); Sigma = c1 F U_mu^dag(x+mu)
             M3<T> F;
             m3_zero(F);
 #pragma unroll 1
             for (int j = 1; j < 4; ++j) {
                 const int nu = (MU + j) & 3;
+                around_nu(g, x, nu, true, S);
 #pragma unroll
                 for (int s = 1; s >= -1; s -= 2) {
-                    Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1);
-                    M3<T> W = m3_mul(path_step<T, NC>(g, U, x, nu, s),
-                                     load_link<T, NC>(U, g.P, MU, sidx(g, xs)));
-                    W = m3_mul(W, load_link<T, NC>(U, g.P, MU, sidx(g, xsm)));
-                    m3_madd(F, W, path_step<T, NC>(g, U, mv(g, xsm, MU, 1), nu, -s));
+                    M3<T> W = m3_mul(step_fwd<T, NC>(g, U, S, nu, s, 0, 0), link_mu<T, NC, MU>(g, U, S, s, 0));
+                    W = m3_mul(W, link_mu<T, NC, MU>(g, U, S, s, 1));
+                    m3_madd(F, W, step_back<T, NC>(g, U, S, nu, s, s, 2));
                 }
             }
-            sig = m3_mul_nd(F, load_link<T, NC>(U, g.P, MU, sidx(g, mv(g, x, MU, 1))));
-            m3_scale(sig, c1);
+            M3<T> t = m3_mul_nd(F, link_at<T, NC>(g, U, MU, S.i0 + S.dmp1, false));
+            m3_axpy(sig, c1, t);
         }
-        {
+        {   // 2. wide backward: Bk = sum fwd(0,-1) U_mu(s,-1) B C; Sigma += c1 U_mu^dag(x-mu) Bk
             M3<T> Bk;
             m3_zero(Bk);
-            const Pt xm = mv(g, x, MU, -1);
 #pragma unroll 1
             for (int j = 1; j < 4; ++j) {
                 const int nu = (MU + j) & 3;
+                around_nu(g, x, nu, true, S);
 #pragma unroll
                 for (int s = 1; s >= -1; s -= 2) {
-                    Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1);
-                    M3<T> BC = m3_mul(load_link<T, NC>(U, g.P, MU, sidx(g, xs)),
-                                      path_step<T, NC>(g, U, xsm, nu, -s));
-                    M3<T> Y = m3_mul(path_step<T, NC>(g, U, xm, nu, s),
-                                     load_link<T, NC>(U, g.P, MU, sidx(g, mv(g, xm, nu, s))));
+                    M3<T> BC = m3_mul(link_mu<T, NC, MU>(g, U, S, s, 0), step_back<T, NC>(g, U, S, nu, s, s, 1));
+                    M3<T> Y = m3_mul(step_fwd<T, NC>(g, U, S, nu, s, 0, -1), link_mu<T, NC, MU>(g, U, S, s, -1));
                     m3_madd(Bk, Y, BC);
                 }
             }
-            M3<T> t = m3_mul_dn(load_link<T, NC>(U, g.P, MU, sidx(g, xm)), Bk);
+            M3<T> t = m3_mul_dn(link_at<T, NC>(g, U, MU, S.i0 + S.dmm1, false), Bk);
             m3_axpy(sig, c1, t);
         }
+        // 3. staples and tall rectangles: Sigma += A (c0 B + c1 fwd(s,0) U_mu(2s,0) back(2s,1)) C
 #pragma unroll 1
         for (int j = 1; j < 4; ++j) {
             const int nu = (MU + j) & 3;
+            around_nu(g, x, nu, true, S);
 #pragma unroll
             for (int s = 1; s >= -1; s -= 2) {
-                Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1), x2s = mv(g, xs, nu, s);
-                M3<T> Tt = m3_mul(path_step<T, NC>(g, U, xs, nu, s),
-                                  load_link<T, NC>(U, g.P, MU, sidx(g, x2s)));
-                Tt = m3_mul(Tt, path_step<T, NC>(g, U, mv(g, x2s, MU, 1), nu, -s));
-                M3<T> N = load_link<T, NC>(U, g.P, MU, sidx(g, xs));
+                M3<T> Tt = m3_mul(step_fwd<T, NC>(g, U, S, nu, s, s, 0), link_mu<T, NC, MU>(g, U, S, 2 * s, 0));
+                Tt = m3_mul(Tt, step_back<T, NC>(g, U, S, nu, s, 2 * s, 1));
+                M3<T> N = link_mu<T, NC, MU>(g, U, S, s, 0);
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
                     N.re[k] = fma(c1, Tt.re[k], c0 * N.re[k]);
                     N.im[k] = fma(c1, Tt.im[k], c0 * N.im[k]);
                 }
-                M3<T> AN = m3_mul(path_step<T, NC>(g, U, x, nu, s), N);
-                m3_madd(sig, AN, path_step<T, NC>(g, U, xsm, nu, -s));
+                M3<T> AN = m3_mul(step_fwd<T, NC>(g, U, S, nu, s, 0, 0), N);
+                m3_madd(sig, AN, step_back<T, NC>(g, U, S, nu, s, s, 1));
             }
         }
     } else {
-        m3_zero(sig);
-#pragma unroll
+#pragma unroll 1
         for (int j = 1; j < 4; ++j) {
             const int nu = (MU + j) & 3;
+            around_nu(g, x, nu, false, S);
 #pragma unroll
             for (int s = 1; s >= -1; s -= 2) {
-                Pt xs = mv(g, x, nu, s), xsm = mv(g, xs, MU, 1);
-                M3<T> AB = m3_mul(path_step<T, NC>(g, U, x, nu, s),
-                                  load_link<T, NC>(U, g.P, MU, sidx(g, xs)));
-                m3_madd(sig, AB, path_step<T, NC>(g, U, xsm, nu, -s));
+                M3<T> AB = m3_mul(step_fwd<T, NC>(g, U, S, nu, s, 0, 0), link_mu<T, NC, MU>(g, U, S, s, 0));
+                m3_madd(sig, AB, step_back<T, NC>(g, U, S, nu, s, s, 1));
             }
         }
         if (c0 != T(1)) m3_scale(sig, c0);

