@@ -38,6 +38,9 @@ REUNIT = 10
 # per update), the updated link written once, its reference label read once.
 BYTES_PER_UPDATE = {(1, 18): 17 * 72 + 1, (1, 12): 17 * 48 + 1, (0, 18): 17 * 144 + 1}
 FLOPS_PER_UPDATE_OVERIMPROVED = 65 * 216 + 600
+# DRAM bytes (read + write) of one class-update launch of this kernel version,
+# from `ncu --set full` on the same command (profiles/k_subsweep_f32_*.md)
+NCU_TRAFFIC_PER_LAUNCH = 937.392384e6 + 54.278144e6
 
 
 def _env_int(k, d):
@@ -249,7 +252,7 @@ def run_ours(args):
     achieved = units * bpu / (per_launch_ms / 1e3) / 1e9
     line["roofline"] = {"kernel": "k_subsweep<float,18,rect>", "bound": "hbm",
                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                        "frac": achieved / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_PER_LAUNCH,
                         "peak_source": src, "per_launch_ms": per_launch_ms,
                         "bytes_per_update": bpu, "updates_per_launch": units,
                         "achieved_tflops": units * FLOPS_PER_UPDATE_OVERIMPROVED
