@@ -239,13 +239,13 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e,
             "gpu_launches": launches}
 
+    peaks, src = _measured_peaks()
     S_last, chk_last = results[-1]
     line["result"] = {"action": S_last, "n_label_diff": chk_last["n_label_diff"],
                       "n_charge_diff": chk_last["n_charge_diff"],
                       "n_near_boundary": chk_last["n_near_boundary"]}
 
     # ---- roofline of the dominant kernel (colour-class update) -------------
-    peaks, src = _measured_peaks()
     per_launch_ms = chain_ms / max(chain_launches, 1)
     units = V // 4
     bpu = BYTES_PER_UPDATE[(1, 18)]
@@ -257,6 +257,13 @@ def run_ours(args):
                         "bytes_per_update": bpu, "updates_per_launch": units,
                         "achieved_tflops": units * FLOPS_PER_UPDATE_OVERIMPROVED
                         / (per_launch_ms / 1e3) / 1e12}
+
+    # ---- the same step with 12-real links (rows 1-2 stored, row 3 rebuilt) ----
+    if not args.no_fp64:
+        try:
+            line["fp32_12real"] = storage12(vs, ctx, stream, labels_dev, args, world, dev, peaks)
+        except Exception as e:
+            line["fp32_12real"] = {"error": repr(e)}
 
     # ---- FP64 plain path, bounded number of sweeps --------------------------
     if not args.no_fp64:
@@ -283,6 +290,39 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def storage12(vs, ctx, stream, labels_dev, args, world, dev, peaks):
+    """One step of the benchmark workload with 12-real link storage."""
+    import torch
+    V = int(np.prod(DIMS))
+    f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK12, stream)
+    vs.vs_load_field(f, labels=labels_dev)
+    vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+    vs.vs_smooth(f, 3, RHO, EPS, U0, reunit_every=REUNIT)
+    vs.vs_load_field(f, labels=labels_dev)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    vs.vs_load_field(f, labels=labels_dev)
+    vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+    vs.vs_set_profiling(f, True)
+    vs.vs_smooth(f, args.sweeps, RHO, EPS, U0, reunit_every=REUNIT, vortex_preserve=True)
+    vs.vs_action(f)
+    chk = vs.vs_vortex_check(f)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    cms, nl = vs.vs_get_profile(f)
+    vs.vs_field_destroy(f)
+    per = cms / nl
+    bpu = BYTES_PER_UPDATE[(1, 12)]
+    ach = V / 4 * bpu / (per / 1e3) / 1e9
+    return {"value": world * 4 * V * args.sweeps / (ms / 1e3), "unit": "link-updates/s",
+            "ms_per_step": ms, "per_launch_ms": per, "bytes_per_update": bpu,
+            "achieved_gbs": ach, "hbm_frac": ach / peaks["hbm_gbs"],
+            "n_label_diff": chk["n_label_diff"]}
 
 
 def fp64_plain(vs, ctx, stream, labels_dev, args, value, world, dev):

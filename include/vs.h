@@ -146,6 +146,20 @@ typedef struct {
 vs_status vs_smooth(vs_field *f, int32_t n_sweeps, double rho, double epsilon, double u0,
                     const vs_anneal *sched, int32_t vortex_preserve, vs_sweep_stats *stats);
 
+/* n_sweeps of annealed U-link smearing with MaxReTr reunitarisation (AUS,
+ * Sec. III Eqs. V and maxReTr; Sec. III.A; the smoother of the paper's CP
+ * and VP recipes): for mu = 0..3, colour 0..3, every link of the class at
+ * once, V = (1 - alpha) U + (alpha / 6) Sigma(eps, u0) with the staples of
+ * Eq. over-improvement, then n_hits passes over the SU(2) subgroups (1,2),
+ * (2,3), (1,3) maximise Re Tr(U V^dag) starting from U (a subgroup with
+ * k = sqrt(det T) = 0 is skipped).  vortex_preserve: Sec. VI test against the
+ * original labels.  FP32: re-unitarise every reunit_every sweeps (0 = never).
+ * alpha = 1 with eps = 1 is cooling.  stats as for vs_smooth (no action).
+ * EINVAL: alpha outside [0, 1], n_hits < 1, non-finite eps, u0 <= 0. */
+vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, double epsilon, double u0,
+                        int32_t n_hits, int32_t reunit_every, int32_t vortex_preserve,
+                        vs_sweep_stats *stats);
+
 /* One colour class (mu, colour) of the annealed schedule, as vs_smooth runs it. */
 vs_status vs_subsweep(vs_field *f, int32_t mu, int32_t colour, double rho, double epsilon,
                       double u0, int32_t vortex_preserve);
@@ -157,6 +171,25 @@ typedef struct {
     int64_t n_near_boundary;      /* links with arg Tr U within 1e-5 rad of a sector edge */
     double min_margin;            /* smallest angular distance of arg Tr U from a sector edge */
 } vs_vortex_report;
+
+typedef struct {
+    double mean_S;                /* <S>/beta, the Wilson action density (Sec. V) */
+    double mean_SR;               /* <S_R>/beta, the reconstructed action from clover F */
+    double Q;                     /* total topological charge sum_x q(x) */
+} vs_observables_out;
+
+/* Smoothness observables, Sec. V: clover field strength F_munu(x) (mean of the
+ * four plaquette leaves at x, F = (C - C^dag)/(2i), traceless, lattice units
+ * -- the coupling of Eq. 1LFST absorbed), the one-loop topological charge
+ * density q(x) = eps_{mu nu rho sigma} Tr(F_munu F_rhosigma)/(32 pi^2)
+ * (Eq. 1LTopQ), and the reconstructed action S_R(x)/beta = 1/72
+ * sum_{mu != nu} Tr(F_munu^2)/2, normalised so that S_R/S -> 1 on smooth
+ * fields (the paper's smoothness condition <S> ~ <S_R>; its printed
+ * normalisation is garbled).  Optional per-site densities S(x)/beta,
+ * S_R(x)/beta, q(x): double [V] in lexicographic order, host or device per
+ * `where`.  Products in the field precision, sums in FP64.  Synchronous. */
+vs_status vs_observables(vs_field *f, vs_observables_out *out, double *S_site, double *SR_site,
+                         double *q_site, int32_t where);
 
 /* Vortex-structure check of the current field against the reference. Synchronous. */
 vs_status vs_vortex_check(vs_field *f, vs_vortex_report *out);
@@ -195,6 +228,15 @@ vs_status vs_action(vs_field *f, double *mean_S);
 vs_status vs_read_field(vs_field *f, double *links_out, int32_t where);
 vs_status vs_read_labels(vs_field *f, int8_t *labels_out, int32_t where);     /* reference */
 vs_status vs_current_labels(vs_field *f, int8_t *labels_out, int32_t where);  /* of current links */
+
+/* Random gauge transformation (Sec. V.D): U_mu(x) -> G(x) U_mu(x) G^dag(x+mu)
+ * for every link, with G: double [V][3][3][2] (lexicographic sites, SU(3)
+ * matrices; host or device per `where`).  The field keeps G: from then on the
+ * vortex-preservation test, the re-unitarisation guard and vs_vortex_check use
+ * the label of G^dag(x) U G(x+mu) against the original labels (Sec. VI, the
+ * test in the original gauge).  Reloading the field drops G.  EINVAL if the
+ * field is already transformed. */
+vs_status vs_gauge_transform(vs_field *f, const double *G, int32_t where);
 
 /* Re-unitarise every link now (FP64 Gram-Schmidt of rows 1-2, row 3 = conj(r1 x r2)). */
 vs_status vs_reunitarise(vs_field *f);

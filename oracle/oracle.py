@@ -15,7 +15,7 @@ __all__ = [
     "label_matrix", "labels", "links_from_labels", "splitmix64", "centrifuge_pair",
     "centrifuge", "overimproved_coeffs", "staple_sum", "expm", "stout_generator",
     "colour", "smooth", "action", "centre_charges", "vortex_check", "gauge_transform",
-    "cool", "ANNEALED", "SIMULTANEOUS",
+    "cool", "aus", "maxretr", "observables", "ANNEALED", "SIMULTANEOUS",
 ]
 
 ANNEALED = 0
@@ -104,12 +104,16 @@ def _declare(L):
         "or_stout_generator": (ctypes.c_int, [P, P]),
         "or_colour": (ctypes.c_int, [P, ctypes.c_int, P]),
         "or_smooth": (ctypes.c_int, [P, P, P, ctypes.c_int, P, dbl, dbl,
-                                     ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P]),
+                                     ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, P]),
         "or_action": (ctypes.c_int, [P, P, P, P]),
         "or_centre_charges": (ctypes.c_int, [P, P, P]),
-        "or_vortex_check": (ctypes.c_int, [P, P, P, P, P, P]),
+        "or_vortex_check": (ctypes.c_int, [P, P, P, P, P, P, P]),
         "or_gauge_transform": (ctypes.c_int, [P, P, P]),
         "or_cool": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "or_aus": (ctypes.c_int, [P, P, P, ctypes.c_int, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                  P, ctypes.c_int, P]),
+        "or_maxretr": (ctypes.c_int, [P, P, ctypes.c_int, P]),
+        "or_observables": (ctypes.c_int, [P, P, P, P, P, P]),
         "or_max_threads": (ctypes.c_int, []),
     }
     for name, (res, args) in sig.items():
@@ -223,7 +227,7 @@ def colour(dims, mu, x):
 
 
 def smooth(dims, links, ref_labels, n_sweeps, rho, eps=1.0, u0=1.0,
-           schedule=ANNEALED, vp=True, nthreads=None, diagnostics=False):
+           schedule=ANNEALED, vp=True, nthreads=None, diagnostics=False, gauge=None):
     """n_sweeps of stout smoothing on a copy of ``links``; returns (links, n_reject),
     plus (candidate margins, rejected mask) of the last sweep with diagnostics=True."""
     d = _dims(dims)
@@ -239,9 +243,11 @@ def smooth(dims, links, ref_labels, n_sweeps, rho, eps=1.0, u0=1.0,
     V = U.size // 36
     cm = np.full((4, V), np.nan) if diagnostics else None
     rj = np.zeros((4, V), dtype=np.int8) if diagnostics else None
+    G = None if gauge is None else _c128(gauge)
     _check(lib().or_smooth(_p(d), _p(U), _p(ref) if ref is not None else None, n_sweeps,
                            _p(rho), eps, u0, schedule, 1 if vp else 0, _p(rej), nt,
-                           _p(cm) if diagnostics else None, _p(rj) if diagnostics else None),
+                           _p(cm) if diagnostics else None, _p(rj) if diagnostics else None,
+                           _p(G) if G is not None else None),
            "smooth")
     if diagnostics:
         return U, rej[:n_sweeps], cm, rj
@@ -267,15 +273,16 @@ def centre_charges(dims, lab):
     return ch
 
 
-def vortex_check(dims, links, ref_labels):
+def vortex_check(dims, links, ref_labels, gauge=None):
     d = _dims(dims)
     U = _c128(links)
     ref = np.ascontiguousarray(ref_labels, dtype=np.int8)
     nd = ctypes.c_int64()
     nc = ctypes.c_int64()
     mm = ctypes.c_double()
+    G = None if gauge is None else _c128(gauge)
     _check(lib().or_vortex_check(_p(d), _p(U), _p(ref), ctypes.byref(nd), ctypes.byref(nc),
-                                 ctypes.byref(mm)), "vortex_check")
+                                 ctypes.byref(mm), _p(G) if G is not None else None), "vortex_check")
     return dict(n_label_diff=nd.value, n_charge_diff=nc.value, min_margin=mm.value)
 
 
@@ -293,3 +300,43 @@ def cool(dims, links, n_sweeps, n_hits=3, nthreads=None):
     nt = max_threads() if nthreads is None else int(nthreads)
     _check(lib().or_cool(_p(d), _p(U), n_sweeps, n_hits, nt), "cool")
     return U
+
+
+def aus(dims, links, ref_labels, n_sweeps, alpha, eps=1.0, u0=1.0, n_hits=3, vp=True, nthreads=None,
+        gauge=None):
+    """n_sweeps of annealed U-link smearing with MaxReTr; returns (links, n_reject)."""
+    d = _dims(dims)
+    U = np.array(links, dtype=np.complex128, order="C", copy=True)
+    ref = None if ref_labels is None else np.ascontiguousarray(ref_labels, dtype=np.int8)
+    rej = np.zeros(max(n_sweeps, 1), dtype=np.int64)
+    nt = max_threads() if nthreads is None else int(nthreads)
+    G = None if gauge is None else _c128(gauge)
+    _check(lib().or_aus(_p(d), _p(U), _p(ref) if ref is not None else None, n_sweeps, alpha, eps,
+                        u0, n_hits, 1 if vp else 0, _p(rej), nt, _p(G) if G is not None else None),
+           "aus")
+    return U, rej[:n_sweeps]
+
+
+def maxretr(U, V, n_hits=3):
+    Uc = _c128(U, (3, 3))
+    Vc = _c128(V, (3, 3))
+    out = np.empty((3, 3), dtype=np.complex128)
+    _check(lib().or_maxretr(_p(Uc), _p(Vc), n_hits, _p(out)), "maxretr")
+    return out
+
+
+def observables(dims, links, per_site=False):
+    """(<S_R>/beta, Q) and, with per_site, the densities S_R(x)/beta and q(x)."""
+    d = _dims(dims)
+    U = _c128(links)
+    V = U.size // 36
+    sr = ctypes.c_double()
+    q = ctypes.c_double()
+    SR = np.empty(V) if per_site else None
+    qs = np.empty(V) if per_site else None
+    _check(lib().or_observables(_p(d), _p(U), ctypes.byref(sr), ctypes.byref(q),
+                                _p(SR) if per_site else None, _p(qs) if per_site else None),
+           "observables")
+    if per_site:
+        return sr.value, q.value, SR, qs
+    return sr.value, q.value

@@ -157,6 +157,26 @@ static double margin_of_trace(cplx t) {
     return m < d3 ? m : d3;
 }
 
+/* Trace tested by vortex preservation (Sec. VI).  In the gauge of the
+ * original field (G == NULL) it is Tr U'; after the random gauge
+ * transformation G it is Tr[G^dag(x) U' G(x + mu)], the candidate transformed
+ * back to the original gauge. */
+static cplx vp_trace(const int L[4], long V, const cplx *G, int mu, const int x[4], const mat3 *Un) {
+    if (!G) return m_trace(Un);
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    y[mu] = (y[mu] + 1) % L[mu];
+    long sx = x[0] + (long)L[0] * (x[1] + (long)L[1] * (x[2] + (long)L[2] * x[3]));
+    long sy = y[0] + (long)L[0] * (y[1] + (long)L[1] * (y[2] + (long)L[2] * y[3]));
+    (void)V;
+    mat3 Gx, Gy;
+    memcpy(&Gx, G + sx * 9, sizeof Gx);
+    memcpy(&Gy, G + sy * 9, sizeof Gy);
+    mat3 Gxd = m_dag(&Gx);
+    mat3 t = m_mul(&Gxd, Un);
+    t = m_mul(&t, &Gy);
+    return m_trace(&t);
+}
+
 int or_label_matrix(const double *M18) {
     mat3 a;
     memcpy(&a, M18, sizeof a);
@@ -417,10 +437,14 @@ enum { OR_ANNEALED = 0, OR_SIMULTANEOUS = 1 };
  *                class concurrently (they are independent by construction).
  *   cand_margin  optional [4][V]: angular distance of arg Tr of each link's
  *                last candidate from the nearest sector edge (last sweep).
- *   rejected     optional [4][V]: 1 where the last sweep rejected the candidate. */
+ *   rejected     optional [4][V]: 1 where the last sweep rejected the candidate.
+ *   gauge        optional [V][3][3] complex: the random gauge transformation
+ *                G applied to the field (Sec. V.D); vortex preservation then
+ *                tests the label of G^dag(x) U' G(x+mu) (Sec. VI). */
 int or_smooth(const int32_t dims[4], double *links, const int8_t *ref_labels, int n_sweeps,
               const double *rho, double eps, double u0, int schedule, int vp,
-              int64_t *n_reject, int nthreads, double *cand_margin, int8_t *rejected) {
+              int64_t *n_reject, int nthreads, double *cand_margin, int8_t *rejected,
+              const double *gauge) {
     lattice g;
     if (lat_init(&g, dims)) return -1;
     if (n_sweeps < 0) return -2;
@@ -430,6 +454,7 @@ int or_smooth(const int32_t dims[4], double *links, const int8_t *ref_labels, in
     double c0, c1;
     or_overimproved_coeffs(eps, u0, &c0, &c1);
     cplx *U = (cplx *)links;
+    const cplx *G = (const cplx *)gauge;
     long *sites = (long *)malloc(sizeof(long) * g.V);
     cplx *old = NULL;
     if (schedule == OR_SIMULTANEOUS) old = (cplx *)malloc(sizeof(cplx) * 9 * 4 * g.V);
@@ -455,9 +480,10 @@ int or_smooth(const int32_t dims[4], double *links, const int8_t *ref_labels, in
                         mat3 Ux = link_get(&g, U, mu, sites[i]);
                         mat3 Un = stout_candidate(&S, &Ux, rho[sw]);
                         const long li = (long)mu * g.V + sites[i];
-                        if (cand_margin) cand_margin[li] = margin_of_trace(m_trace(&Un));
+                        const cplx tr = vp_trace(g.L, g.V, G, mu, x, &Un);
+                        if (cand_margin) cand_margin[li] = margin_of_trace(tr);
                         if (rejected) rejected[li] = 0;
-                        if (vp && label_of_trace(m_trace(&Un)) != ref_labels[li]) {
+                        if (vp && label_of_trace(tr) != ref_labels[li]) {
                             rej += 1;
                             if (rejected) rejected[li] = 1;
                             continue;
@@ -479,9 +505,10 @@ int or_smooth(const int32_t dims[4], double *links, const int8_t *ref_labels, in
                 if (staple_sum(&g, old, mu, x, c0, c1, &S)) { err |= 1; continue; }
                 mat3 Ux = link_get(&g, old, mu, s);
                 mat3 Un = stout_candidate(&S, &Ux, rho[sw]);
-                if (cand_margin) cand_margin[i] = margin_of_trace(m_trace(&Un));
+                const cplx tr = vp_trace(g.L, g.V, G, mu, x, &Un);
+                if (cand_margin) cand_margin[i] = margin_of_trace(tr);
                 if (rejected) rejected[i] = 0;
-                if (vp && label_of_trace(m_trace(&Un)) != ref_labels[i]) {
+                if (vp && label_of_trace(tr) != ref_labels[i]) {
                     rej += 1;
                     if (rejected) rejected[i] = 1;
                     continue;
@@ -529,6 +556,87 @@ int or_action(const int32_t dims[4], const double *links, double *mean_S, double
     return 0;
 }
 
+/* Clover-leaf field strength (Sec. V, Eq. 1LFST), in lattice units (the
+ * coupling of Eq. 1LFST absorbed into F): C_munu(x) is the mean of the four
+ * plaquette leaves of the (mu, nu) plane that start and end at x, all with
+ * the same orientation; F_munu = (C - C^dag)/(2i) with its trace removed. */
+static mat3 clover_F(const lattice *g, const cplx *U, const int x[4], int mu, int nu) {
+    const pstep leaves[4][4] = {{{mu, +1}, {nu, +1}, {mu, -1}, {nu, -1}},
+                                {{nu, +1}, {mu, -1}, {nu, -1}, {mu, +1}},
+                                {{mu, -1}, {nu, -1}, {mu, +1}, {nu, +1}},
+                                {{nu, -1}, {mu, +1}, {nu, +1}, {mu, -1}}};
+    mat3 C = m_zero();
+    for (int l = 0; l < 4; ++l) {
+        int end[4];
+        mat3 P = path_product(g, U, x, leaves[l], 4, end);
+        m_axpy(&C, 0.25, &P);
+    }
+    mat3 Cd = m_dag(&C);
+    mat3 F;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) F.m[i][j] = (C.m[i][j] - Cd.m[i][j]) / (2.0 * I);
+    cplx tr = m_trace(&F) / 3.0;
+    for (int i = 0; i < 3; ++i) F.m[i][i] -= tr;
+    return F;
+}
+
+static int levi_civita(int a, int b, int c, int d) {
+    int p[4] = {a, b, c, d}, sgn = 1;
+    for (int i = 0; i < 4; ++i)
+        for (int j = i + 1; j < 4; ++j) {
+            if (p[i] == p[j]) return 0;
+            if (p[i] > p[j]) sgn = -sgn;
+        }
+    return sgn;
+}
+
+/* Smoothness observables, Sec. V:
+ *   q(x) = 1/(32 pi^2) eps_{mu nu rho sigma} Tr[F_munu(x) F_rhosigma(x)]  (Eq. 1LTopQ),
+ *   S_R(x)/beta = 1/72 sum_{mu != nu} (1/2) Tr[F_munu(x) F_munu(x)],
+ * the reconstructed action normalised so that S_R -> S on smooth fields
+ * (P = exp(i theta) gives Re Tr(1 - P) = Tr(theta^2)/2 + O(theta^4) and
+ * F = theta + O(theta^3)); the paper's print of this normalisation is garbled.
+ * Outputs the means <S_R>/beta and the total charge Q = sum_x q(x), and
+ * optionally the densities. */
+int or_observables(const int32_t dims[4], const double *links, double *mean_SR, double *Q,
+                   double *SR_site, double *q_site) {
+    lattice g;
+    if (lat_init(&g, dims)) return -1;
+    const cplx *U = (const cplx *)links;
+    double sr_tot = 0.0, q_tot = 0.0;
+    for (long s = 0; s < g.V; ++s) {
+        int x[4];
+        lat_coords(&g, s, x);
+        mat3 F[4][4];
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = 0; nu < 4; ++nu)
+                F[mu][nu] = mu == nu ? m_zero() : clover_F(&g, U, x, mu, nu);
+        double sr = 0.0, qx = 0.0;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = 0; nu < 4; ++nu) {
+                if (mu == nu) continue;
+                mat3 FF = m_mul(&F[mu][nu], &F[mu][nu]);
+                sr += 0.5 * creal(m_trace(&FF));
+                for (int rh = 0; rh < 4; ++rh)
+                    for (int si = 0; si < 4; ++si) {
+                        int e = levi_civita(mu, nu, rh, si);
+                        if (!e) continue;
+                        mat3 P = m_mul(&F[mu][nu], &F[rh][si]);
+                        qx += e * creal(m_trace(&P));
+                    }
+            }
+        sr /= 72.0;
+        qx /= 32.0 * OR_PI * OR_PI;
+        if (SR_site) SR_site[s] = sr;
+        if (q_site) q_site[s] = qx;
+        sr_tot += sr;
+        q_tot += qx;
+    }
+    *mean_SR = sr_tot / (double)g.V;
+    *Q = q_tot;
+    return 0;
+}
+
 /* Vortex flux through plaquette (mu, nu) at x from labels:
  * P = Z_mu(x) Z_nu(x+mu) Z_mu^dag(x+nu) Z_nu^dag(x) = exp(2 pi i p / 3), Sec. I. */
 static int centre_charge(const lattice *g, const int8_t *lab, const int x[4], int mu, int nu) {
@@ -557,15 +665,26 @@ int or_centre_charges(const int32_t dims[4], const int8_t *labels, int8_t *charg
 
 /* Counts over the field: links whose label differs from the reference, and
  * plaquettes whose centre charge differs from the reference charge; plus the
- * smallest angular distance of any arg Tr U from a sector boundary. */
+ * smallest angular distance of any arg Tr U from a sector boundary.  With a
+ * gauge transformation G the labels are those of G^dag(x) U G(x+mu). */
 int or_vortex_check(const int32_t dims[4], const double *links, const int8_t *ref_labels,
-                    int64_t *n_label_diff, int64_t *n_charge_diff, double *min_margin) {
+                    int64_t *n_label_diff, int64_t *n_charge_diff, double *min_margin,
+                    const double *gauge) {
     lattice g;
     if (lat_init(&g, dims)) return -1;
     int8_t *lab = (int8_t *)malloc(4 * g.V);
     double *mar = (double *)malloc(sizeof(double) * 4 * g.V);
     if (!lab || !mar) { free(lab); free(mar); return -5; }
-    or_labels(dims, links, lab, mar);
+    const cplx *U = (const cplx *)links;
+    for (int mu = 0; mu < 4; ++mu)
+        for (long s = 0; s < g.V; ++s) {
+            int x[4];
+            lat_coords(&g, s, x);
+            mat3 a = link_get(&g, U, mu, s);
+            cplx tr = vp_trace(g.L, g.V, (const cplx *)gauge, mu, x, &a);
+            lab[(long)mu * g.V + s] = (int8_t)label_of_trace(tr);
+            mar[(long)mu * g.V + s] = margin_of_trace(tr);
+        }
     int64_t nd = 0, nc = 0;
     double mm = 1e300;
     for (long i = 0; i < 4 * g.V; ++i) {
@@ -615,61 +734,111 @@ int or_gauge_transform(const int32_t dims[4], double *links, const double *G /*[
 }
 
 /* ------------------------------------------------------------------------ */
-/* MaxReTr cooling (Sec. III, Eqs. maxReTr, def_L1, def_T1), input recipe    */
+/* Annealed U-link smearing with MaxReTr (Sec. III, Eqs. V, maxReTr,         */
+/* def_L1, def_T1); cooling is its alpha = 1 case                           */
 /* ------------------------------------------------------------------------ */
 
-/* Cooling = annealed MaxReTr at alpha = 1 with standard plaquette staples:
- * V = Sigma / 6, and for each link three passes over the SU(2) subgroups
- * (1,2), (2,3), (1,3): L = U V^dag, T from L's 2x2 block, T^c = T^dag / k with
- * k = sqrt(det T), U <- T^c U.  A link with k = 0 is left unchanged.  Used to
- * generate the cooled hot-start inputs; same colour order as the smoother. */
-int or_cool(const int32_t dims[4], double *links, int n_sweeps, int n_hits, int nthreads) {
+/* One MaxReTr update of link U towards the blocked matrix Vb: n_hits passes
+ * over the SU(2) subgroups (1,2), (2,3), (1,3).  For subgroup (p,q):
+ * L = U Vb^dag, T = [[a, b], [-conj b, conj a]] with a = (L_pp + conj L_qq)/2,
+ * b = (L_pq - conj L_qp)/2, k = sqrt(det T) = sqrt(|a|^2 + |b|^2),
+ * T^c = T^dag / k embedded in SU(3), U <- T^c U.
+ * The singular case (Sec. III.A): on vortex fields the staple sums take
+ * discrete values and k can vanish exactly, where the paper notes that
+ * rounding noise then picks an essentially random link.  Reading used: a
+ * subgroup step with k <= 1e-6 of the block's scale
+ * sqrt(|L_pp|^2 + |L_qq|^2 + |L_pq|^2 + |L_qp|^2) leaves the link unchanged,
+ * which makes the result independent of rounding. */
+static mat3 maxretr(const mat3 *U, const mat3 *Vb, int n_hits) {
+    static const int sub[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    mat3 Vd = m_dag(Vb);
+    mat3 Ux = *U;
+    for (int h = 0; h < n_hits; ++h)
+        for (int t = 0; t < 3; ++t) {
+            int p = sub[t][0], q = sub[t][1];
+            mat3 L = m_mul(&Ux, &Vd);
+            cplx al = 0.5 * (L.m[p][p] + conj(L.m[q][q]));
+            cplx be = 0.5 * (L.m[p][q] - conj(L.m[q][p]));
+            double k = sqrt(creal(al * conj(al)) + creal(be * conj(be)));
+            double scale = sqrt(creal(L.m[p][p] * conj(L.m[p][p])) + creal(L.m[q][q] * conj(L.m[q][q])) +
+                                creal(L.m[p][q] * conj(L.m[p][q])) + creal(L.m[q][p] * conj(L.m[q][p])));
+            if (!(k > 1e-6 * scale)) continue;
+            mat3 Tc = m_eye();
+            Tc.m[p][p] = conj(al) / k;
+            Tc.m[p][q] = -be / k;
+            Tc.m[q][p] = conj(be) / k;
+            Tc.m[q][q] = al / k;
+            Ux = m_mul(&Tc, &Ux);
+        }
+    return Ux;
+}
+
+/* n_sweeps of annealed U-link smearing in place, in the colour order of
+ * or_smooth: V = (1 - alpha) U + (alpha / 6) Sigma(eps, u0) (Eq. V with the
+ * staples of Eq. over-improvement), the link replaced by maxretr(U, V).
+ * vp / ref_labels / n_reject / gauge as in or_smooth (Sec. VI).  alpha = 1 with
+ * eps = 1 is cooling: V does not depend on U. */
+int or_aus(const int32_t dims[4], double *links, const int8_t *ref_labels, int n_sweeps, double alpha,
+           double eps, double u0, int n_hits, int vp, int64_t *n_reject, int nthreads,
+           const double *gauge) {
     lattice g;
     if (lat_init(&g, dims)) return -1;
     for (int d = 0; d < 4; ++d)
         if (g.L[d] % 4) return -3;
+    if (vp && !ref_labels) return -4;
+    double c0, c1;
+    or_overimproved_coeffs(eps, u0, &c0, &c1);
     cplx *U = (cplx *)links;
+    const cplx *G = (const cplx *)gauge;
     long *sites = (long *)malloc(sizeof(long) * g.V);
     if (!sites) return -5;
-    static const int sub[3][2] = {{0, 1}, {1, 2}, {0, 2}};
     int err = 0;
-    for (int sw = 0; sw < n_sweeps; ++sw)
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        int64_t rej = 0;
         for (int mu = 0; mu < 4; ++mu)
             for (int c = 0; c < 4; ++c) {
                 long n = class_sites(&g, mu, c, sites);
 #ifdef _OPENMP
-#pragma omp parallel for num_threads(nthreads < 1 ? 1 : nthreads) schedule(static) reduction(| : err)
+#pragma omp parallel for num_threads(nthreads < 1 ? 1 : nthreads) schedule(static) reduction(+ : rej) reduction(| : err)
 #endif
                 for (long i = 0; i < n; ++i) {
                     int x[4];
                     lat_coords(&g, sites[i], x);
                     mat3 S;
-                    if (staple_sum(&g, U, mu, x, 1.0, 0.0, &S)) { err |= 1; continue; }
-                    mat3 Vb = S;
-                    for (int a = 0; a < 3; ++a)
-                        for (int b = 0; b < 3; ++b) Vb.m[a][b] /= 6.0;
-                    mat3 Vd = m_dag(&Vb);
+                    if (staple_sum(&g, U, mu, x, c0, c1, &S)) { err |= 1; continue; }
                     mat3 Ux = link_get(&g, U, mu, sites[i]);
-                    for (int h = 0; h < n_hits; ++h)
-                        for (int t = 0; t < 3; ++t) {
-                            int p = sub[t][0], q = sub[t][1];
-                            mat3 L = m_mul(&Ux, &Vd);
-                            cplx al = 0.5 * (L.m[p][p] + conj(L.m[q][q]));
-                            cplx be = 0.5 * (L.m[p][q] - conj(L.m[q][p]));
-                            double k = sqrt(creal(al * conj(al)) + creal(be * conj(be)));
-                            if (!(k > 0.0)) continue;
-                            mat3 Tc = m_eye();
-                            Tc.m[p][p] = conj(al) / k;
-                            Tc.m[p][q] = -be / k;
-                            Tc.m[q][p] = conj(be) / k;
-                            Tc.m[q][q] = al / k;
-                            Ux = m_mul(&Tc, &Ux);
-                        }
-                    link_put(&g, U, mu, sites[i], &Ux);
+                    mat3 Vb = m_zero();
+                    m_axpy(&Vb, 1.0 - alpha, &Ux);
+                    m_axpy(&Vb, alpha / 6.0, &S);
+                    mat3 Un = maxretr(&Ux, &Vb, n_hits);
+                    if (vp && label_of_trace(vp_trace(g.L, g.V, G, mu, x, &Un)) !=
+                                  ref_labels[(long)mu * g.V + sites[i]]) {
+                        rej += 1;
+                        continue;
+                    }
+                    link_put(&g, U, mu, sites[i], &Un);
                 }
             }
+        if (n_reject) n_reject[sw] = rej;
+    }
     free(sites);
     return err ? -6 : 0;
+}
+
+/* Cooling: annealed MaxReTr at alpha = 1 with the plaquette staples,
+ * V = Sigma / 6 (used to generate the cooled hot-start inputs). */
+int or_cool(const int32_t dims[4], double *links, int n_sweeps, int n_hits, int nthreads) {
+    return or_aus(dims, links, NULL, n_sweeps, 1.0, 1.0, 1.0, n_hits, 0, NULL, nthreads, NULL);
+}
+
+/* One MaxReTr update of a single matrix (for the pins). */
+int or_maxretr(const double *U18, const double *V18, int n_hits, double *out18) {
+    mat3 U, Vb, R;
+    memcpy(&U, U18, sizeof U);
+    memcpy(&Vb, V18, sizeof Vb);
+    R = maxretr(&U, &Vb, n_hits);
+    memcpy(out18, &R, sizeof R);
+    return 0;
 }
 
 int or_max_threads(void) {

@@ -170,6 +170,7 @@ extern "C" void vs_field_destroy(vs_field *f) {
     dev_free(f->ctx, f->U);
     dev_free(f->ctx, f->ref);
     dev_free(f->ctx, f->cur);
+    dev_free(f->ctx, f->G);
     dev_free(f->ctx, f->partials);
     dev_free(f->ctx, f->scratch);
     dev_free(f->ctx, f->sweep_counts);
@@ -260,6 +261,7 @@ extern "C" vs_status vs_load_field(vs_field *f, const double *links, const int8_
     if (where == VS_HOST) CK(cudaStreamSynchronize(f->stream));
     f->loaded = true;
     f->sweeps_done = 0;
+    f->gauge_on = false;
     return VS_OK;
 }
 
@@ -322,18 +324,66 @@ extern "C" vs_status vs_centrifuge(vs_field *f, double omega, uint64_t seed) {
     return VS_OK;
 }
 
+static AusParams make_aus_params(vs_field *f, double alpha, double eps, double u0, int n_hits, int vp) {
+    AusParams a;
+    memset(&a, 0, sizeof a);
+    a.g = f->g;
+    a.U = f->U;
+    a.ref = f->ref;
+    a.G = f->gauge_on ? f->G : nullptr;
+    a.n_threads = f->g.V / 4;
+    a.alpha = alpha;
+    a.c0 = (5.0 - 2.0 * eps) / 3.0;
+    a.c1 = (eps - 1.0) / (12.0 * u0 * u0);
+    a.alpha_f = (float)a.alpha;
+    a.c0_f = (float)a.c0;
+    a.c1_f = (float)a.c1;
+    a.n_hits = n_hits;
+    a.vp = vp ? 1 : 0;
+    return a;
+}
+
 extern "C" vs_status vs_load_cooled(vs_field *f, uint64_t seed, int32_t n_cool) {
     if (!f) return fail(VS_EINVAL, "vs_load_cooled: NULL field");
     if (n_cool < 0) return fail(VS_EINVAL, "vs_load_cooled: n_cool < 0");
     CK(cudaSetDevice(f->ctx->opt.device));
     const int p = f->prec == VS_FP32;
     CK(launch_haar(p, f->nc, f->g, seed, f->U, f->stream));
+    AusParams a = make_aus_params(f, 1.0, 1.0, 1.0, 3, 0);
     for (int s = 0; s < n_cool; ++s)
         for (int mu = 0; mu < 4; ++mu)
-            for (int c = 0; c < 4; ++c) CK(launch_cool_class(p, f->nc, f->g, mu, c, f->U, f->stream));
+            for (int c = 0; c < 4; ++c) {
+                a.colour = c;
+                CK(launch_aus_class(p, f->nc, false, mu, a, f->stream));
+            }
     CK(launch_project(p, f->nc, f->g, f->U, f->ref, f->stream));
     f->loaded = true;
     f->sweeps_done = 0;
+    f->gauge_on = false;
+    return VS_OK;
+}
+
+extern "C" vs_status vs_gauge_transform(vs_field *f, const double *G, int32_t where) {
+    if (!f || !G) return fail(VS_EINVAL, "vs_gauge_transform: NULL argument");
+    if (where != VS_HOST && where != VS_DEVICE) return fail(VS_EINVAL, "vs_gauge_transform: bad `where`");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_gauge_transform: field not loaded");
+    if (f->gauge_on) return fail(VS_EINVAL, "vs_gauge_transform: field already transformed (reload first)");
+    CK(cudaSetDevice(f->ctx->opt.device));
+    const size_t V = f->g.V;
+    if (!f->G) {
+        f->G = dev_alloc(f->ctx, V * 18 * (f->prec == VS_FP64 ? 8 : 4));
+        if (!f->G) return fail(VS_ENOMEM, "vs_gauge_transform: allocation failed");
+    }
+    const double *src = G;
+    if (where == VS_HOST) {
+        vs_status st = ensure_scratch(f, V * 18 * sizeof(double));
+        if (st) return st;
+        CK(cudaMemcpyAsync(f->scratch, G, V * 18 * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+        src = (const double *)f->scratch;
+    }
+    CK(launch_gauge(f->prec == VS_FP32, f->nc, f->g, src, f->G, f->U, f->stream));
+    if (where == VS_HOST) CK(cudaStreamSynchronize(f->stream));
+    f->gauge_on = true;
     return VS_OK;
 }
 
@@ -372,9 +422,13 @@ static SubsweepParams make_params(vs_field *f, double rho, double eps, double u0
     p.U = f->U;
     p.Usrc = f->U;
     p.ref = f->ref;
+    p.G = f->gauge_on ? f->G : nullptr;
     p.rho = rho;
     p.c0 = (5.0 - 2.0 * eps) / 3.0;
     p.c1 = (eps - 1.0) / (12.0 * u0 * u0);
+    p.rho_f = (float)p.rho;
+    p.c0_f = (float)p.c0;
+    p.c1_f = (float)p.c1;
     p.vp = vp ? 1 : 0;
     return p;
 }
@@ -479,7 +533,8 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
         }
         if (f->profiling) CK(cudaEventRecord(f->events[2 * s + 1], f->stream));
         if (f->prec == VS_FP32 && a.reunit_every > 0 && (f->sweeps_done + s + 1) % a.reunit_every == 0)
-            CK(launch_reunit(1, f->nc, f->g, f->U, vp ? f->ref : nullptr, f->stream));
+            CK(launch_reunit(1, f->nc, f->g, f->U, vp ? f->ref : nullptr, f->stream,
+                             f->gauge_on ? f->G : nullptr));
         if (want_stats && a.action_every > 0 && (s + 1) % a.action_every == 0)
             CK(launch_action(f->prec == VS_FP32, f->nc, f->g, f->U, f->partials, f->sweep_actions + s, f->stream));
     }
@@ -527,6 +582,58 @@ extern "C" vs_status vs_smooth(vs_field *f, int32_t n_sweeps, double rho, double
     return check_device_error(f);
 }
 
+extern "C" vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, double epsilon, double u0,
+                                   int32_t n_hits, int32_t reunit_every, int32_t vortex_preserve,
+                                   vs_sweep_stats *stats) {
+    if (!f) return fail(VS_EINVAL, "vs_smooth_aus: NULL field");
+    if (n_sweeps < 0 || n_hits < 1 || reunit_every < 0) return fail(VS_EINVAL, "vs_smooth_aus: bad count");
+    if (!std::isfinite(alpha) || !(alpha >= 0.0 && alpha <= 1.0) || !std::isfinite(epsilon) || !(u0 > 0))
+        return fail(VS_EINVAL, "vs_smooth_aus: need 0 <= alpha <= 1, finite eps, u0 > 0");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_smooth_aus: field not loaded");
+    CK(cudaSetDevice(f->ctx->opt.device));
+    const bool rect = epsilon != 1.0;
+    const int p = f->prec == VS_FP32;
+    if (stats && f->sweep_cap < n_sweeps) {
+        CK(cudaStreamSynchronize(f->stream));
+        dev_free(f->ctx, f->sweep_counts);
+        dev_free(f->ctx, f->sweep_actions);
+        f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, 2 * sizeof(unsigned long long) * n_sweeps);
+        f->sweep_actions = (double *)dev_alloc(f->ctx, sizeof(double) * n_sweeps);
+        if (!f->sweep_counts || !f->sweep_actions) {
+            f->sweep_cap = 0;
+            return fail(VS_ENOMEM, "vs_smooth_aus: stats allocation failed");
+        }
+        f->sweep_cap = n_sweeps;
+    }
+    if (stats && n_sweeps > 0)
+        CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_sweeps, f->stream));
+    AusParams a = make_aus_params(f, alpha, epsilon, u0, n_hits, vortex_preserve);
+    for (int s = 0; s < n_sweeps; ++s) {
+        a.counters = stats ? f->sweep_counts + 2 * s : nullptr;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int c = 0; c < 4; ++c) {
+                a.colour = c;
+                CK(launch_aus_class(p, f->nc, rect, mu, a, f->stream));
+            }
+        if (f->prec == VS_FP32 && reunit_every > 0 && (f->sweeps_done + s + 1) % reunit_every == 0)
+            CK(launch_reunit(1, f->nc, f->g, f->U, vortex_preserve ? f->ref : nullptr, f->stream,
+                             f->gauge_on ? f->G : nullptr));
+    }
+    f->sweeps_done += n_sweeps;
+    if (!stats) return VS_OK;
+    std::vector<unsigned long long> cnt(2 * (size_t)n_sweeps);
+    if (n_sweeps > 0)
+        CK(cudaMemcpyAsync(cnt.data(), f->sweep_counts, cnt.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    for (int s = 0; s < n_sweeps; ++s) {
+        memset(&stats[s], 0, sizeof stats[s]);
+        stats[s].n_reject = (int64_t)cnt[2 * s];
+        stats[s].n_accept = 4ll * f->g.V - stats[s].n_reject;
+    }
+    return check_device_error(f);
+}
+
 // ---------------------------------------------------------------------------
 // Observables
 // ---------------------------------------------------------------------------
@@ -540,13 +647,46 @@ extern "C" vs_status vs_action(vs_field *f, double *mean_S) {
     return VS_OK;
 }
 
+extern "C" vs_status vs_observables(vs_field *f, vs_observables_out *out, double *S_site, double *SR_site,
+                                    double *q_site, int32_t where) {
+    if (!f || !out) return fail(VS_EINVAL, "vs_observables: NULL argument");
+    if (where != VS_HOST && where != VS_DEVICE) return fail(VS_EINVAL, "vs_observables: bad `where`");
+    CK(cudaSetDevice(f->ctx->opt.device));
+    const size_t V = f->g.V;
+    double *dS = S_site, *dSR = SR_site, *dq = q_site;
+    if (where == VS_HOST && (S_site || SR_site || q_site)) {
+        vs_status st = ensure_scratch(f, 3 * V * sizeof(double));
+        if (st) return st;
+        double *sc = (double *)f->scratch;
+        dS = S_site ? sc : nullptr;
+        dSR = SR_site ? sc + V : nullptr;
+        dq = q_site ? sc + 2 * V : nullptr;
+    }
+    // 3 x 400 partials fit in the 1216 + 512 doubles after f->partials; results after them
+    double *res = f->partials + 1200;
+    CK(launch_observables(f->prec == VS_FP32, f->nc, f->g, f->U, f->partials, res, dS, dSR, dq, f->stream));
+    double h[3];
+    CK(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, f->stream));
+    if (where == VS_HOST) {
+        if (S_site) CK(cudaMemcpyAsync(S_site, dS, V * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+        if (SR_site) CK(cudaMemcpyAsync(SR_site, dSR, V * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+        if (q_site) CK(cudaMemcpyAsync(q_site, dq, V * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+    }
+    CK(cudaStreamSynchronize(f->stream));
+    out->mean_S = h[0];
+    out->mean_SR = h[1];
+    out->Q = h[2];
+    return VS_OK;
+}
+
 extern "C" vs_status vs_vortex_check(vs_field *f, vs_vortex_report *out) {
     if (!f || !out) return fail(VS_EINVAL, "vs_vortex_check: NULL argument");
     CK(cudaSetDevice(f->ctx->opt.device));
     unsigned long long *cnt = f->d_counts + 2;      // [3] counts, [1] margin bits
     CK(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), f->stream));
     CK(cudaMemsetAsync(cnt + 3, 0x7f, sizeof(unsigned long long), f->stream));
-    CK(launch_vortex(f->prec == VS_FP32, f->nc, f->g, f->U, f->ref, f->cur, cnt, cnt + 3, f->stream));
+    CK(launch_vortex(f->prec == VS_FP32, f->nc, f->g, f->U, f->ref, f->cur, cnt, cnt + 3, f->stream,
+                     f->gauge_on ? f->G : nullptr));
     unsigned long long h[4];
     CK(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, f->stream));
     CK(cudaStreamSynchronize(f->stream));

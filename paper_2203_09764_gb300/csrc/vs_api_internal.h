@@ -39,6 +39,8 @@ struct vs_field {
     void *U = nullptr;
     int8_t *ref = nullptr;
     int8_t *cur = nullptr;
+    void *G = nullptr;              // random gauge transformation (18 reals per site)
+    bool gauge_on = false;          // links are in the random gauge G
     double *partials = nullptr;
     double *d_result = nullptr;
     unsigned long long *d_counts = nullptr;

@@ -216,6 +216,21 @@ __device__ __forceinline__ void m3_scale(M3<T> &r, T s) {
 //   double, 18 reals: 9 planes of double2 (one complex entry each)
 // A plane holding w reals per site starts at (reals before it) * P and site i
 // sits at w * i inside it, so every load is one aligned 8- or 16-byte vector.
+// row 2 = conj(row 0 x row 1): the third row of an SU(3) matrix from the first two
+template <class T>
+__device__ __forceinline__ void rebuild_row2(M3<T> &m) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        T cr = m.re[j1] * m.re[3 + j2] - m.im[j1] * m.im[3 + j2]
+             - (m.re[j2] * m.re[3 + j1] - m.im[j2] * m.im[3 + j1]);
+        T ci = m.re[j1] * m.im[3 + j2] + m.im[j1] * m.re[3 + j2]
+             - (m.re[j2] * m.im[3 + j1] + m.im[j2] * m.re[3 + j1]);
+        m.re[6 + j] = cr;
+        m.im[6 + j] = -ci;
+    }
+}
+
 template <class T, int NC>
 __device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P, int mu, int i) {
     const T *base = U + (long long)mu * NC * P;
@@ -237,19 +252,7 @@ __device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P,
             m.re[e] = v.x; m.im[e] = v.y;
         }
     }
-    if (NC == 12) {
-        // row 2 = conj(row 0 x row 1)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-            T cr = m.re[j1] * m.re[3 + j2] - m.im[j1] * m.im[3 + j2]
-                 - (m.re[j2] * m.re[3 + j1] - m.im[j2] * m.im[3 + j1]);
-            T ci = m.re[j1] * m.im[3 + j2] + m.im[j1] * m.re[3 + j2]
-                 - (m.re[j2] * m.im[3 + j1] + m.im[j2] * m.re[3 + j1]);
-            m.re[6 + j] = cr;
-            m.im[6 + j] = -ci;
-        }
-    }
+    if (NC == 12) rebuild_row2(m);
     return m;
 }
 
@@ -283,6 +286,38 @@ __device__ __forceinline__ int z3_label(T a, T b) {
     if (b > T(0)) return 1;
     if (b < T(0)) return -1;
     return a < T(0) ? 1 : 0;
+}
+
+// Trace seen by the vortex-preservation test (Sec. VI): Tr U for the original
+// gauge (G == nullptr); after a random gauge transformation G,
+// Tr[G^dag(x) U G(x+mu)] = sum_jk U_jk (G(x+mu) G^dag(x))_kj.  G is stored as
+// 18 reals per site in the link layout, plane position i.
+template <class T>
+__device__ __forceinline__ void vp_trace(const T *__restrict__ G, long long P, int i_x, int i_xmu,
+                                         const M3<T> &u, T &a, T &b) {
+    if (!G) {
+        a = u.re[0] + u.re[4] + u.re[8];
+        b = u.im[0] + u.im[4] + u.im[8];
+        return;
+    }
+    const M3<T> gx = load_link<T, 18>(G, P, 0, i_x), gy = load_link<T, 18>(G, P, 0, i_xmu);
+    T sr = T(0), si = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // M_kj = sum_l gy_kl conj(gx_jl)
+            T mr = T(0), mi = T(0);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                mr = fma(gy.re[3 * k + l], gx.re[3 * j + l], fma(gy.im[3 * k + l], gx.im[3 * j + l], mr));
+                mi = fma(gy.im[3 * k + l], gx.re[3 * j + l], fma(-gy.re[3 * k + l], gx.im[3 * j + l], mi));
+            }
+            sr = fma(u.re[3 * j + k], mr, fma(-u.im[3 * j + k], mi, sr));
+            si = fma(u.re[3 * j + k], mi, fma(u.im[3 * j + k], mr, si));
+        }
+    a = sr;
+    b = si;
 }
 
 // --------------------------------------------------------------------------

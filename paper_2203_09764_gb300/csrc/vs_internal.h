@@ -13,9 +13,11 @@ struct SubsweepParams {
     void *U;             // field being updated (in place for the annealed schedule)
     const void *Usrc;    // staple source: == U (annealed) or the previous field (simultaneous)
     const int8_t *ref;   // reference labels [4][P]
+    const void *G;       // random gauge transformation (18 reals per site) or null
     int colour;          // 0..3, or -1: every site of direction mu
     int n_threads;
     double rho, c0, c1;
+    float rho_f, c0_f, c1_f;   // the same, rounded once on the host for the FP32 kernels
     int vp;
     unsigned long long *counters;  // [0] rejects, [1] FP64 exponentials (may be null)
 };
@@ -23,6 +25,27 @@ struct SubsweepParams {
 // process-wide count of direct kernel launches
 void count_launches(int n);
 long long launches();
+
+// One colour class of annealed U-link smearing with MaxReTr (Sec. III):
+// V = (1 - alpha) U + (alpha / 6) Sigma(eps); n_hits passes over the SU(2)
+// subgroups; optional vortex preservation.  alpha = 1, eps = 1 is cooling.
+struct AusParams {
+    Geo g;
+    void *U;
+    const int8_t *ref;
+    const void *G;       // random gauge transformation or null
+    int colour;
+    int n_threads;
+    double alpha, c0, c1;
+    float alpha_f, c0_f, c1_f;
+    int n_hits;
+    int vp;
+    unsigned long long *counters;  // [0] rejects (may be null)
+};
+
+cudaError_t launch_aus_f18(bool rect, int mu, const AusParams &p, cudaStream_t st);
+cudaError_t launch_aus_f12(bool rect, int mu, const AusParams &p, cudaStream_t st);
+cudaError_t launch_aus_d18(bool rect, int mu, const AusParams &p, cudaStream_t st);
 
 cudaError_t launch_subsweep_f18(bool rect, int mu, const SubsweepParams &p, cudaStream_t st);
 cudaError_t launch_subsweep_f12(bool rect, int mu, const SubsweepParams &p, cudaStream_t st);
@@ -44,16 +67,24 @@ cudaError_t launch_centrifuge(int prec, int nc, const Geo &g, const int8_t *ref,
 int action_partials(const Geo &g);
 cudaError_t launch_action(int prec, int nc, const Geo &g, const void *U, double *partials,
                           double *out, cudaStream_t st);
+// <S>/beta, <S_R>/beta and Q into out[0..2]; partials: 3 x 400 doubles;
+// optional per-site densities in lexicographic order
+cudaError_t launch_observables(int prec, int nc, const Geo &g, const void *U, double *partials, double *out,
+                               double *S_site, double *SR_site, double *q_site, cudaStream_t st);
 // counts[0] label diffs, counts[1] charge diffs, counts[2] near-boundary links;
 // margin_bits: min angular margin as the bit pattern of a non-negative double
 cudaError_t launch_vortex(int prec, int nc, const Geo &g, const void *U, const int8_t *ref,
                           int8_t *cur, unsigned long long *counts,
-                          unsigned long long *margin_bits, cudaStream_t st);
-cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, const int8_t *ref, cudaStream_t st);
+                          unsigned long long *margin_bits, cudaStream_t st, const void *G = nullptr);
+cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, const int8_t *ref, cudaStream_t st,
+                          const void *G = nullptr);
+// random gauge transformation: store G (FP64 host layout [V][3][3][2], on the
+// device) in the field precision, and transform every link
+cudaError_t launch_gauge(int prec, int nc, const Geo &g, const double *G_lex, void *Gs, void *U,
+                         cudaStream_t st);
 cudaError_t launch_debug_expm(int prec, const double *X, int n, double *E, cudaStream_t st);
 cudaError_t launch_haar(int prec, int nc, const Geo &g, uint64_t seed, void *U, cudaStream_t st);
-cudaError_t launch_cool_class(int prec, int nc, const Geo &g, int mu, int colour, void *U,
-                              cudaStream_t st);
+cudaError_t launch_aus_class(int prec, int nc, bool rect, int mu, const AusParams &p, cudaStream_t st);
 cudaError_t launch_project(int prec, int nc, const Geo &g, void *U, int8_t *ref, cudaStream_t st);
 
 }  // namespace vs

@@ -183,6 +183,113 @@ __global__ void __launch_bounds__(kThreads) k_action(Geo g, const T *__restrict_
     if (threadIdx.x == 0) partials[blockIdx.x] = b;
 }
 
+// ---------------------------------------------------------------------------
+// Smoothness observables, Sec. V: clover F_munu (the mean of the four leaves of
+// the plane at x, F = (C - C^dag)/(2i), traceless), per site
+//   S(x)/beta   = 1/72 sum_{mu != nu} Re Tr(1 - P_munu)
+//   S_R(x)/beta = 1/72 sum_{mu != nu} Tr(F_munu^2) / 2
+//   q(x)        = [Tr(F01 F23) - Tr(F02 F13) + Tr(F03 F12)] / (4 pi^2)
+// (the eps-sum of Eq. 1LTopQ collapsed to its three pairings x 8 / (32 pi^2)).
+// ---------------------------------------------------------------------------
+
+template <class T, int NC>
+__device__ __forceinline__ M3<T> clover_F(const Geo &g, const T *__restrict__ U, const Pt &x, int i, int mu,
+                                          int nu, T &plaq_retr) {
+    const Pt xpm = mv(g, x, mu, 1), xpn = mv(g, x, nu, 1), xmm = mv(g, x, mu, -1), xmn = mv(g, x, nu, -1);
+    const int ipm = sidx(g, xpm), ipn = sidx(g, xpn), imm = sidx(g, xmm), imn = sidx(g, xmn);
+    const int ipnmm = sidx(g, mv(g, xpn, mu, -1)), immmn = sidx(g, mv(g, xmm, nu, -1));
+    const int imnpm = sidx(g, mv(g, xmn, mu, 1));
+    M3<T> C, L;
+    // leaf 1: +mu +nu -mu -nu
+    L = m3_mul(load_link<T, NC>(U, g.P, mu, i), load_link<T, NC>(U, g.P, nu, ipm));
+    L = m3_mul_nd(L, load_link<T, NC>(U, g.P, mu, ipn));
+    L = m3_mul_nd(L, load_link<T, NC>(U, g.P, nu, i));
+    plaq_retr = L.re[0] + L.re[4] + L.re[8];
+    C = L;
+    // leaf 2: +nu -mu -nu +mu
+    L = m3_mul_nd(load_link<T, NC>(U, g.P, nu, i), load_link<T, NC>(U, g.P, mu, ipnmm));
+    L = m3_mul_nd(L, load_link<T, NC>(U, g.P, nu, imm));
+    m3_madd(C, L, load_link<T, NC>(U, g.P, mu, imm));
+    // leaf 3: -mu -nu +mu +nu
+    L = m3_mul_dn(load_link<T, NC>(U, g.P, mu, imm), m3_dag(load_link<T, NC>(U, g.P, nu, immmn)));
+    L = m3_mul(L, load_link<T, NC>(U, g.P, mu, immmn));
+    m3_madd(C, L, load_link<T, NC>(U, g.P, nu, imn));
+    // leaf 4: -nu +mu +nu -mu
+    L = m3_mul_dn(load_link<T, NC>(U, g.P, nu, imn), load_link<T, NC>(U, g.P, mu, imn));
+    L = m3_mul(L, load_link<T, NC>(U, g.P, nu, imnpm));
+    L = m3_mul_nd(L, load_link<T, NC>(U, g.P, mu, i));
+    for (int k = 0; k < 9; ++k) { C.re[k] += L.re[k]; C.im[k] += L.im[k]; }
+    // F = (C - C^dag) / (2i) / 4, traceless
+    M3<T> F;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T dr = C.re[3 * j + k] - C.re[3 * k + j], di = C.im[3 * j + k] + C.im[3 * k + j];
+            F.re[3 * j + k] = T(0.125) * di;
+            F.im[3 * j + k] = -T(0.125) * dr;
+        }
+    const T tr = (F.re[0] + F.re[4] + F.re[8]) / T(3);
+    F.re[0] -= tr;
+    F.re[4] -= tr;
+    F.re[8] -= tr;
+    return F;
+}
+
+// Tr(A B) for Hermitian A, B: sum_jk A_jk conj(B_jk), real
+template <class T>
+__device__ __forceinline__ double tr_herm(const M3<T> &A, const M3<T> &B) {
+    double s = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s += (double)A.re[k] * B.re[k] + (double)A.im[k] * B.im[k];
+    return s;
+}
+
+template <class T, int NC>
+__global__ void __launch_bounds__(kThreads) k_observables(Geo g, const T *__restrict__ U, double *partials,
+                                                           double *S_site, double *SR_site, double *q_site) {
+    double aS = 0, aSR = 0, aQ = 0;
+    const int pairs[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
+    const double sgn[3] = {1.0, -1.0, 1.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.V; i += gridDim.x * blockDim.x) {
+        const Pt x = site_of_index(g, i);
+        double s = 0, sr = 0, q = 0;
+        for (int pp = 0; pp < 3; ++pp) {
+            T r1, r2;
+            const M3<T> Fa = clover_F<T, NC>(g, U, x, i, pairs[pp][0], pairs[pp][1], r1);
+            const M3<T> Fb = clover_F<T, NC>(g, U, x, i, pairs[pp][2], pairs[pp][3], r2);
+            s += (3.0 - (double)r1) + (3.0 - (double)r2);
+            sr += tr_herm(Fa, Fa) + tr_herm(Fb, Fb);
+            q += sgn[pp] * tr_herm(Fa, Fb);
+        }
+        s *= 2.0 / 72.0;
+        sr /= 72.0;
+        q /= 4.0 * 9.869604401089358;
+        const int lx = lexidx(g, x);
+        if (S_site) S_site[lx] = s;
+        if (SR_site) SR_site[lx] = sr;
+        if (q_site) q_site[lx] = q;
+        aS += s;
+        aSR += sr;
+        aQ += q;
+    }
+    const double b0 = block_sum(aS), b1 = block_sum(aSR), b2 = block_sum(aQ);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x] = b0;
+        partials[3 * blockIdx.x + 1] = b1;
+        partials[3 * blockIdx.x + 2] = b2;
+    }
+}
+
+__global__ void k_sum_partials3(const double *__restrict__ partials, int n, double invV, double *out) {
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[3 * i + c];
+        const double b = block_sum(acc);
+        if (threadIdx.x == 0) out[c] = c < 2 ? b * invV : b;
+    }
+}
+
 __global__ void k_sum_partials(const double *__restrict__ partials, int n, double scale, double *out) {
     double acc = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
@@ -201,14 +308,16 @@ __device__ __forceinline__ void count_warp(unsigned long long *ctr, bool pred) {
 
 template <class T, int NC>
 __global__ void k_vortex_links(Geo g, const T *__restrict__ U, const int8_t *__restrict__ ref,
-                               int8_t *cur, unsigned long long *counts, unsigned long long *mbits) {
+                               int8_t *cur, unsigned long long *counts, unsigned long long *mbits,
+                               const T *__restrict__ G) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool diff = false, near = false;
     double margin = 1e300;
     if (l < 4ll * g.V) {
         int mu = (int)(l / g.V), i = (int)(l % g.V);
         M3<T> m = load_link<T, NC>(U, g.P, mu, i);
-        T a = m.re[0] + m.re[4] + m.re[8], b = m.im[0] + m.im[4] + m.im[8];
+        T a, b;
+        vp_trace<T>(G, g.P, i, G ? sidx(g, mv(g, site_of_index(g, i), mu, 1)) : i, m, a, b);
         int lab = z3_label<T>(a, b);
         cur[(long long)mu * g.P + i] = (int8_t)lab;
         diff = lab != ref[(long long)mu * g.P + i];
@@ -259,7 +368,7 @@ __global__ void k_vortex_charges(Geo g, const int8_t *__restrict__ ref, const in
 // ---------------------------------------------------------------------------
 
 template <class T, int NC>
-__global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref) {
+__global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref, const T *__restrict__ G) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= 4ll * g.V) return;
     int mu = (int)(l / g.V), i = (int)(l % g.V);
@@ -300,9 +409,11 @@ __global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref) {
         m.re[6 + j] = cr;
         m.im[6 + j] = -ci;
     }
-    if (ref && z3_label<T>(m.re[0] + m.re[4] + m.re[8], m.im[0] + m.im[4] + m.im[8]) !=
-                   (int)ref[(long long)mu * g.P + i])
-        return;
+    if (ref) {
+        T a, b;
+        vp_trace<T>(G, g.P, i, G ? sidx(g, mv(g, site_of_index(g, i), mu, 1)) : i, m, a, b);
+        if (z3_label<T>(a, b) != (int)ref[(long long)mu * g.P + i]) return;
+    }
     store_link<T, NC>(U, g.P, mu, i, m);
 }
 
@@ -393,47 +504,30 @@ __global__ void k_haar(Geo g, uint64_t seed, T *U) {
     store_link<T, NC>(U, g.P, mu, sidx(g, site_of_lex(g, s)), m);
 }
 
-// One colour class of annealed MaxReTr cooling (Sec. III, alpha = 1):
-// V = Sigma / 6; three passes over the SU(2) subgroups (0,1), (1,2), (0,2):
-// L = U V^dag, alpha = (L_pp + conj L_qq)/2, beta = (L_pq - conj L_qp)/2,
-// k = sqrt(|alpha|^2 + |beta|^2), T^c = [[conj alpha, -beta], [conj beta, alpha]] / k,
-// U <- T^c U.  k = 0 leaves the link unchanged.
-template <class T, int NC, int MU>
-__global__ void __launch_bounds__(128) k_cool(Geo g, int colour, T *U) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.V / 4) return;
-    Pt x = class_site<MU>(g, colour, t);
-    int i = sidx(g, x);
-    M3<T> sig = staple_sum<T, NC, false, MU>(g, U, x, T(1), T(0));
-    m3_scale(sig, T(1) / T(6));
-    M3<T> Vd = m3_dag(sig);
-    M3<T> u = load_link<T, NC>(U, g.P, MU, i);
-    const int sp[3] = {0, 1, 0}, sq[3] = {1, 2, 2};
-    for (int hit = 0; hit < 3; ++hit) {
+// Random gauge transformation (Sec. V.D): store G(x) (FP64 [V][3][3][2] in
+// lexicographic site order) as 18 reals per site in the link layout, then
+// U_mu(x) -> G(x) U_mu(x) G^dag(x + mu) for every link.
+template <class T>
+__global__ void k_store_gauge(Geo g, const double *__restrict__ Glex, T *Gs) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    const double *q = Glex + 18ll * s;
+    M3<T> m;
 #pragma unroll
-        for (int sgi = 0; sgi < 3; ++sgi) {
-            const int p = sp[sgi], q = sq[sgi];
-            M3<T> L = m3_mul(u, Vd);
-            T ar = T(0.5) * (L.re[4 * p] + L.re[4 * q]), ai = T(0.5) * (L.im[4 * p] - L.im[4 * q]);
-            T br = T(0.5) * (L.re[3 * p + q] - L.re[3 * q + p]), bi = T(0.5) * (L.im[3 * p + q] + L.im[3 * q + p]);
-            T k = sqrt(ar * ar + ai * ai + br * br + bi * bi);
-            if (!(k > T(0))) continue;
-            T ik = T(1) / k;
-            // T^c block: [[conj a, -b], [conj b, a]] / k acting on rows p, q
-            T c00r = ar * ik, c00i = -ai * ik, c01r = -br * ik, c01i = -bi * ik;
-            T c10r = br * ik, c10i = -bi * ik, c11r = ar * ik, c11i = ai * ik;
-#pragma unroll
-            for (int col = 0; col < 3; ++col) {
-                T upr = u.re[3 * p + col], upi = u.im[3 * p + col];
-                T uqr = u.re[3 * q + col], uqi = u.im[3 * q + col];
-                u.re[3 * p + col] = c00r * upr - c00i * upi + c01r * uqr - c01i * uqi;
-                u.im[3 * p + col] = c00r * upi + c00i * upr + c01r * uqi + c01i * uqr;
-                u.re[3 * q + col] = c10r * upr - c10i * upi + c11r * uqr - c11i * uqi;
-                u.im[3 * q + col] = c10r * upi + c10i * upr + c11r * uqi + c11i * uqr;
-            }
-        }
-    }
-    store_link<T, NC>(U, g.P, MU, i, u);
+    for (int k = 0; k < 9; ++k) { m.re[k] = T(q[2 * k]); m.im[k] = T(q[2 * k + 1]); }
+    store_link<T, 18>(Gs, g.P, 0, sidx(g, site_of_lex(g, s)), m);
+}
+
+template <class T, int NC>
+__global__ void k_gauge_links(Geo g, const T *__restrict__ Gs, T *U) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), i = (int)(l % g.V);
+    const int iy = sidx(g, mv(g, site_of_index(g, i), mu, 1));
+    M3<T> u = load_link<T, NC>(U, g.P, mu, i);
+    u = m3_mul(load_link<T, 18>(Gs, g.P, 0, i), u);
+    u = m3_mul_nd(u, load_link<T, 18>(Gs, g.P, 0, iy));
+    store_link<T, NC>(U, g.P, mu, i, u);
 }
 
 // Z(3) projection of every link: reference label from arg Tr U, link -> exp(2 pi i n/3) I.
@@ -543,22 +637,45 @@ cudaError_t launch_action(int prec, int nc, const Geo &g, const void *U, double 
     return cudaGetLastError();
 }
 
+cudaError_t launch_observables(int prec, int nc, const Geo &g, const void *U, double *partials, double *out,
+                               double *S_site, double *SR_site, double *q_site, cudaStream_t st) {
+    int b = nblocks(g.V);
+    b = b < 400 ? b : 400;
+    if (prec == 0)
+        k_observables<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, partials, S_site, SR_site, q_site);
+    else if (nc == 18)
+        k_observables<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, partials, S_site, SR_site, q_site);
+    else
+        k_observables<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, partials, S_site, SR_site, q_site);
+    k_sum_partials3<<<1, 1024, 0, st>>>(partials, b, 1.0 / (double)g.V, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vortex(int prec, int nc, const Geo &g, const void *U, const int8_t *ref, int8_t *cur,
-                          unsigned long long *counts, unsigned long long *mbits, cudaStream_t st) {
+                          unsigned long long *counts, unsigned long long *mbits, cudaStream_t st,
+                          const void *G) {
     int b = nblocks(4ll * g.V);
-    if (prec == 0) k_vortex_links<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, ref, cur, counts, mbits);
-    else if (nc == 18) k_vortex_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits);
-    else k_vortex_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits);
+    if (prec == 0)
+        k_vortex_links<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, ref, cur, counts, mbits,
+                                                           (const double *)G);
+    else if (nc == 18)
+        k_vortex_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits,
+                                                          (const float *)G);
+    else
+        k_vortex_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, ref, cur, counts, mbits,
+                                                          (const float *)G);
     k_vortex_charges<<<nblocks(g.V), kThreads, 0, st>>>(g, ref, cur, counts);
     count_launches(2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, const int8_t *ref, cudaStream_t st) {
+cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, const int8_t *ref, cudaStream_t st,
+                          const void *G) {
     int b = nblocks(4ll * g.V);
-    if (prec == 0) k_reunit<double, 18><<<b, kThreads, 0, st>>>(g, (double *)U, ref);
-    else if (nc == 18) k_reunit<float, 18><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
-    else k_reunit<float, 12><<<b, kThreads, 0, st>>>(g, (float *)U, ref);
+    if (prec == 0) k_reunit<double, 18><<<b, kThreads, 0, st>>>(g, (double *)U, ref, (const double *)G);
+    else if (nc == 18) k_reunit<float, 18><<<b, kThreads, 0, st>>>(g, (float *)U, ref, (const float *)G);
+    else k_reunit<float, 12><<<b, kThreads, 0, st>>>(g, (float *)U, ref, (const float *)G);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -579,23 +696,26 @@ cudaError_t launch_haar(int prec, int nc, const Geo &g, uint64_t seed, void *U, 
     return cudaGetLastError();
 }
 
-template <class T, int NC>
-static cudaError_t cool_tpl(const Geo &g, int mu, int colour, T *U, cudaStream_t st) {
-    int b = nblocks(g.V / 4, 128);
-    switch (mu) {
-        case 0: k_cool<T, NC, 0><<<b, 128, 0, st>>>(g, colour, U); break;
-        case 1: k_cool<T, NC, 1><<<b, 128, 0, st>>>(g, colour, U); break;
-        case 2: k_cool<T, NC, 2><<<b, 128, 0, st>>>(g, colour, U); break;
-        default: k_cool<T, NC, 3><<<b, 128, 0, st>>>(g, colour, U); break;
-    }
-    count_launches(1);
-    return cudaGetLastError();
+cudaError_t launch_aus_class(int prec, int nc, bool rect, int mu, const AusParams &p, cudaStream_t st) {
+    if (prec == 0) return launch_aus_d18(rect, mu, p, st);
+    if (nc == 18) return launch_aus_f18(rect, mu, p, st);
+    return launch_aus_f12(rect, mu, p, st);
 }
 
-cudaError_t launch_cool_class(int prec, int nc, const Geo &g, int mu, int colour, void *U, cudaStream_t st) {
-    if (prec == 0) return cool_tpl<double, 18>(g, mu, colour, (double *)U, st);
-    if (nc == 18) return cool_tpl<float, 18>(g, mu, colour, (float *)U, st);
-    return cool_tpl<float, 12>(g, mu, colour, (float *)U, st);
+cudaError_t launch_gauge(int prec, int nc, const Geo &g, const double *G_lex, void *Gs, void *U,
+                         cudaStream_t st) {
+    if (prec == 0) {
+        k_store_gauge<double><<<nblocks(g.V), kThreads, 0, st>>>(g, G_lex, (double *)Gs);
+        k_gauge_links<double, 18><<<nblocks(4ll * g.V), kThreads, 0, st>>>(g, (const double *)Gs, (double *)U);
+    } else {
+        k_store_gauge<float><<<nblocks(g.V), kThreads, 0, st>>>(g, G_lex, (float *)Gs);
+        if (nc == 18)
+            k_gauge_links<float, 18><<<nblocks(4ll * g.V), kThreads, 0, st>>>(g, (const float *)Gs, (float *)U);
+        else
+            k_gauge_links<float, 12><<<nblocks(4ll * g.V), kThreads, 0, st>>>(g, (const float *)Gs, (float *)U);
+    }
+    count_launches(2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_project(int prec, int nc, const Geo &g, void *U, int8_t *ref, cudaStream_t st) {

@@ -294,15 +294,19 @@ __device__ __forceinline__ M3<T> stout_candidate(const M3<T> &sig, const M3<T> &
     return m3_mul(Mx, Ux);
 }
 
+#ifndef VS_SUBSWEEP_THREADS
+#define VS_SUBSWEEP_THREADS 256
+#endif
 #ifndef VS_SUBSWEEP_MINB
-#define VS_SUBSWEEP_MINB 4
+#define VS_SUBSWEEP_MINB (512 / VS_SUBSWEEP_THREADS)
 #endif
 
 // One thread per link of the colour class (or of direction MU when colour < 0).
-// FP32: at most 65536 / (128 * VS_SUBSWEEP_MINB) registers per thread, so
-// VS_SUBSWEEP_MINB blocks of 128 threads fit on an SM.
+// FP32: at most 65536 / (VS_SUBSWEEP_THREADS * VS_SUBSWEEP_MINB) registers per
+// thread (128 by default), so VS_SUBSWEEP_MINB blocks fit on an SM (16 warps).
 template <class T, int NC, bool RECT, int MU>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1) k_subsweep(SubsweepParams a) {
+__global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1)
+    k_subsweep(SubsweepParams a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
     bool reject = false, used64 = false;
@@ -311,12 +315,17 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1) k_
         Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
         const int i = sidx(g, x);
         const T *Us = static_cast<const T *>(a.Usrc);
-        M3<T> sig = staple_sum<T, NC, RECT, MU>(g, Us, x, T(a.c0), T(a.c1));
+        const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
+        const T rho = sizeof(T) == 4 ? T(a.rho_f) : T(a.rho);
+        M3<T> sig = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
         M3<T> Ux = load_link<T, NC>(Us, g.P, MU, i);
-        M3<T> Un = stout_candidate<T>(sig, Ux, T(a.rho), used64);
+        M3<T> Un = stout_candidate<T>(sig, Ux, rho, used64);
+        // 12-real storage keeps rows 0-1 and rebuilds row 2 on every load: the
+        // test must see that matrix, not the one computed here
+        if (NC == 12) rebuild_row2(Un);
         if (a.vp) {
-            T tr_re = Un.re[0] + Un.re[4] + Un.re[8];
-            T tr_im = Un.im[0] + Un.im[4] + Un.im[8];
+            T tr_re, tr_im;
+            vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re, tr_im);
             reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
         }
         if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Un);
@@ -328,6 +337,100 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1) k_
             if (rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
             if (fb) atomicAdd(&a.counters[1], (unsigned long long)__popc(fb));
         }
+    }
+}
+
+}  // namespace vs
+
+namespace vs {
+
+// MaxReTr towards the blocked matrix Vb (Eqs. maxReTr, def_L1, def_T1): for
+// each SU(2) subgroup (p,q) in the order (0,1), (1,2), (0,2), n_hits times,
+// only the 2x2 block of L = U Vb^dag is formed; a = (L_pp + conj L_qq)/2,
+// b = (L_pq - conj L_qp)/2, k = sqrt(|a|^2 + |b|^2), and rows p, q of U are
+// replaced by T^c U with T^c = [[conj a, -b], [conj b, a]] / k.  A singular
+// subgroup, k <= 1e-6 of the block's scale (Sec. III.A: exact on vortex
+// fields, where rounding would otherwise pick the link), leaves it unchanged.
+template <class T>
+__device__ __forceinline__ void maxretr(M3<T> &u, const M3<T> &Vb, int n_hits) {
+    for (int hit = 0; hit < n_hits; ++hit) {
+#pragma unroll
+        for (int sgi = 0; sgi < 3; ++sgi) {
+            const int p = sgi == 1 ? 1 : 0, q = sgi == 0 ? 1 : 2;
+            // L_rc = sum_k u_rk conj(Vb_ck)
+            T lr[2][2], li[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int rr = r ? q : p, cc = c ? q : p;
+                    T sr = T(0), si = T(0);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        sr = fma(u.re[3 * rr + k], Vb.re[3 * cc + k], sr);
+                        sr = fma(u.im[3 * rr + k], Vb.im[3 * cc + k], sr);
+                        si = fma(u.im[3 * rr + k], Vb.re[3 * cc + k], si);
+                        si = fma(-u.re[3 * rr + k], Vb.im[3 * cc + k], si);
+                    }
+                    lr[r][c] = sr;
+                    li[r][c] = si;
+                }
+            const T ar = T(0.5) * (lr[0][0] + lr[1][1]), ai = T(0.5) * (li[0][0] - li[1][1]);
+            const T br = T(0.5) * (lr[0][1] - lr[1][0]), bi = T(0.5) * (li[0][1] + li[1][0]);
+            const T k2 = ar * ar + ai * ai + br * br + bi * bi;
+            // singular subgroup (Sec. III.A): k <= 1e-6 of the block's scale
+            const T sc2 = lr[0][0] * lr[0][0] + li[0][0] * li[0][0] + lr[1][1] * lr[1][1] + li[1][1] * li[1][1] +
+                          lr[0][1] * lr[0][1] + li[0][1] * li[0][1] + lr[1][0] * lr[1][0] + li[1][0] * li[1][0];
+            if (!(k2 > T(1e-12) * sc2)) continue;
+            const T ik = T(1) / sqrt(k2);
+            const T c00r = ar * ik, c00i = -ai * ik, c01r = -br * ik, c01i = -bi * ik;
+            const T c10r = br * ik, c10i = -bi * ik, c11r = ar * ik, c11i = ai * ik;
+#pragma unroll
+            for (int col = 0; col < 3; ++col) {
+                const T upr = u.re[3 * p + col], upi = u.im[3 * p + col];
+                const T uqr = u.re[3 * q + col], uqi = u.im[3 * q + col];
+                u.re[3 * p + col] = c00r * upr - c00i * upi + c01r * uqr - c01i * uqi;
+                u.im[3 * p + col] = c00r * upi + c00i * upr + c01r * uqi + c01i * uqr;
+                u.re[3 * q + col] = c10r * upr - c10i * upi + c11r * uqr - c11i * uqi;
+                u.im[3 * q + col] = c10r * upi + c10i * upr + c11r * uqi + c11i * uqr;
+            }
+        }
+    }
+}
+
+template <class T, int NC, bool RECT, int MU>
+__global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1)
+    k_aus(AusParams a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false;
+    if (active) {
+        const Geo &g = a.g;
+        const Pt x = class_site<MU>(g, a.colour, t);
+        const int i = sidx(g, x);
+        T *U = static_cast<T *>(a.U);
+        const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
+        const T al = sizeof(T) == 4 ? T(a.alpha_f) : T(a.alpha);
+        M3<T> Vb = staple_sum<T, NC, RECT, MU>(g, U, x, c0, c1);
+        M3<T> u = load_link<T, NC>(U, g.P, MU, i);
+        const T w6 = al / T(6), w1 = T(1) - al;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            Vb.re[k] = fma(w1, u.re[k], w6 * Vb.re[k]);
+            Vb.im[k] = fma(w1, u.im[k], w6 * Vb.im[k]);
+        }
+        maxretr<T>(u, Vb, a.n_hits);
+        if (NC == 12) rebuild_row2(u);
+        if (a.vp) {
+            T tr_re, tr_im;
+            vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, u, tr_re, tr_im);
+            reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
+        }
+        if (!reject) store_link<T, NC>(U, g.P, MU, i, u);
+    }
+    if (a.counters) {
+        unsigned rb = __ballot_sync(0xffffffffu, reject);
+        if ((threadIdx.x & 31) == 0 && rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
     }
 }
 

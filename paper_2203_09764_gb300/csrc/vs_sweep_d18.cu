@@ -4,4 +4,7 @@ namespace vs {
 cudaError_t launch_subsweep_d18(bool rect, int mu, const SubsweepParams &p, cudaStream_t st) {
     return launch_subsweep_tpl<double, 18>(rect, mu, p, st);
 }
+cudaError_t launch_aus_d18(bool rect, int mu, const AusParams &p, cudaStream_t st) {
+    return launch_aus_tpl<double, 18>(rect, mu, p, st);
+}
 }  // namespace vs

@@ -10,10 +10,36 @@ namespace vs {
 
 template <class T, int NC>
 cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cudaStream_t st) {
-    const int threads = 128;
+    const int threads = VS_SUBSWEEP_THREADS;
     const int blocks = (p.n_threads + threads - 1) / threads;
     if (blocks == 0) return cudaSuccess;
 #define VS_LAUNCH(R, M) k_subsweep<T, NC, R, M><<<blocks, threads, 0, st>>>(p)
+    if (rect) {
+        switch (mu) {
+            case 0: VS_LAUNCH(true, 0); break;
+            case 1: VS_LAUNCH(true, 1); break;
+            case 2: VS_LAUNCH(true, 2); break;
+            default: VS_LAUNCH(true, 3); break;
+        }
+    } else {
+        switch (mu) {
+            case 0: VS_LAUNCH(false, 0); break;
+            case 1: VS_LAUNCH(false, 1); break;
+            case 2: VS_LAUNCH(false, 2); break;
+            default: VS_LAUNCH(false, 3); break;
+        }
+    }
+#undef VS_LAUNCH
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <class T, int NC>
+cudaError_t launch_aus_tpl(bool rect, int mu, const AusParams &p, cudaStream_t st) {
+    const int threads = VS_SUBSWEEP_THREADS;
+    const int blocks = (p.n_threads + threads - 1) / threads;
+    if (blocks == 0) return cudaSuccess;
+#define VS_LAUNCH(R, M) k_aus<T, NC, R, M><<<blocks, threads, 0, st>>>(p)
     if (rect) {
         switch (mu) {
             case 0: VS_LAUNCH(true, 0); break;

@@ -59,6 +59,10 @@ class vs_vortex_report(ctypes.Structure):
                 ("min_margin", ctypes.c_double)]
 
 
+class vs_observables_out(ctypes.Structure):
+    _fields_ = [("mean_S", ctypes.c_double), ("mean_SR", ctypes.c_double), ("Q", ctypes.c_double)]
+
+
 class vs_field_desc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 4), ("precision", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("n_sites", ctypes.c_int64),
@@ -105,14 +109,18 @@ _SIGS = {
     "vs_centrifuge": (ctypes.c_int32, [P, ctypes.c_double, ctypes.c_uint64]),
     "vs_smooth": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.POINTER(vs_anneal), ctypes.c_int32, P]),
+    "vs_smooth_aus": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]),
     "vs_subsweep": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "vs_vortex_check": (ctypes.c_int32, [P, ctypes.POINTER(vs_vortex_report)]),
     "vs_action": (ctypes.c_int32, [P, ctypes.POINTER(ctypes.c_double)]),
+    "vs_observables": (ctypes.c_int32, [P, ctypes.POINTER(vs_observables_out), P, P, P, ctypes.c_int32]),
     "vs_read_field": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_read_labels": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_current_labels": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_reunitarise": (ctypes.c_int32, [P]),
+    "vs_gauge_transform": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_synchronize": (ctypes.c_int32, [P]),
     "vs_set_profiling": (ctypes.c_int32, [P, ctypes.c_int32]),
     "vs_get_profile": (ctypes.c_int32, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
@@ -297,6 +305,17 @@ def vs_smooth(f, n_sweeps, rho, epsilon=1.0, u0=1.0, kind=VS_ANNEALED, rho_per_s
                  action=(s.action if s.has_action else None)) for s in st[:int(n_sweeps)]]
 
 
+def vs_smooth_aus(f, n_sweeps, alpha, epsilon=-0.25, u0=1.0, n_hits=3, reunit_every=10,
+                  vortex_preserve=True, stats=False):
+    st = (vs_sweep_stats * max(int(n_sweeps), 1))() if stats else None
+    _check(lib.vs_smooth_aus(f, int(n_sweeps), float(alpha), float(epsilon), float(u0), int(n_hits),
+                             int(reunit_every), 1 if vortex_preserve else 0,
+                             ctypes.cast(st, ctypes.c_void_p) if stats else None))
+    if not stats:
+        return None
+    return [dict(n_accept=s.n_accept, n_reject=s.n_reject) for s in st[:int(n_sweeps)]]
+
+
 def vs_subsweep(f, mu, colour, rho, epsilon=1.0, u0=1.0, vortex_preserve=True):
     _check(lib.vs_subsweep(f, int(mu), int(colour), float(rho), float(epsilon), float(u0),
                            1 if vortex_preserve else 0))
@@ -324,6 +343,30 @@ def vs_action(f):
     v = ctypes.c_double()
     _check(lib.vs_action(f, ctypes.byref(v)))
     return v.value
+
+
+def vs_observables(f, per_site=False):
+    """Dict with mean_S, mean_SR, Q; with per_site also the densities S, S_R, q
+    (numpy [V], lexicographic sites)."""
+    o = vs_observables_out()
+    if per_site:
+        V = _field_sites(f)
+        dens = [np.empty(V) for _ in range(3)]
+        ptrs = [ctypes.c_void_p(a.ctypes.data) for a in dens]
+        _check(lib.vs_observables(f, ctypes.byref(o), ptrs[0], ptrs[1], ptrs[2], VS_HOST))
+    else:
+        _check(lib.vs_observables(f, ctypes.byref(o), None, None, None, VS_HOST))
+    r = dict(mean_S=o.mean_S, mean_SR=o.mean_SR, Q=o.Q)
+    if per_site:
+        r.update(S=dens[0], S_R=dens[1], q=dens[2])
+    return r
+
+
+def correlation(a, b):
+    """C_XY = <a b> / sqrt(<a^2> <b^2>) of two densities (Sec. VII, Eq. correlation_s)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.mean(a * b) / np.sqrt(np.mean(a * a) * np.mean(b * b)))
 
 
 def _field_sites(f):
@@ -355,6 +398,14 @@ def vs_current_labels(f, out=None):
     p, where = _ptr(out)
     _check(lib.vs_current_labels(f, p, where))
     return out
+
+
+def vs_gauge_transform(f, G):
+    """Apply the random gauge transformation G (complex [V][3][3], numpy or torch CUDA)."""
+    if isinstance(G, np.ndarray):
+        G = np.ascontiguousarray(G, dtype=np.complex128)
+    p, where = _ptr(G)
+    _check(lib.vs_gauge_transform(f, p, where))
 
 
 def vs_reunitarise(f):

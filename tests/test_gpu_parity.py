@@ -268,3 +268,143 @@ def test_subsweep_matches_single_link_oracle(ctx):
             else:
                 assert np.array_equal(Ug[m, s], U[m, s])
     assert n_upd == V // 4
+
+
+# --------------------------------------------------------------------------
+# Annealed U-link smearing with MaxReTr (Sec. III): the CP / VP / AS recipes
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("recipe", ["VP", "CP", "AS"])
+def test_aus_maxretr_fp64_matches_oracle(ctx, recipe):
+    """AUS with MaxReTr, over-improved eps = -0.25, FP64 against the oracle,
+    per-sweep reject counts identical:
+      VP / CP: centrifuge (w = 0.02), alpha = 0.02, with / without vortex
+               preservation, 10 sweeps (in the original gauge);
+      AS:      random gauge, alpha = 0.7, no preservation, 3 sweeps (large steps
+               on the rough vortex field amplify rounding quickly).
+    On an exactly Z(3) field in its own gauge, MaxReTr candidates can land
+    exactly on a sector edge, where the decision is a rounding tie; the AS
+    recipe runs in a random gauge, as in the paper, which has no exact ties."""
+    dims = (8, 8, 8, 8)
+    lab = cooled_labels(dims, 2)
+    if recipe == "AS":
+        G = synth.random_gauge(dims, 43)
+        U0 = O.gauge_transform(dims, O.links_from_labels(dims, lab), G)
+        alpha, vp, n = 0.7, False, 3
+    else:
+        G = None
+        U0 = O.centrifuge(dims, lab, 0.02, 1234)
+        alpha, vp, n = 0.02, recipe == "VP", 10
+    Uo, rej = O.aus(dims, U0, lab, n, alpha, eps=-0.25, vp=vp, gauge=G)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=lab)
+    if recipe == "AS":
+        vs.vs_gauge_transform(f, G)
+    else:
+        vs.vs_centrifuge(f, 0.02, 1234)
+    assert max_abs(vs.vs_read_field(f), U0) < 1e-14
+    st = vs.vs_smooth_aus(f, n, alpha, -0.25, vortex_preserve=vp, stats=True)
+    Ug = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    # alpha = 0.7 on the rough field divides by small k = sqrt(det T) in many
+    # subgroup steps, which magnifies rounding differences (observed 1.4e-9
+    # after 3 sweeps); alpha = 0.02 stays at the 1e-11 FP64 level
+    assert max_abs(Ug, Uo) < (1e-8 if recipe == "AS" else 1e-11)
+    assert [s["n_reject"] for s in st] == list(rej)
+
+
+def test_aus_cooling_equals_hot_start_generator_step(ctx):
+    """alpha = 1, eps = 1 is cooling: one AUS sweep on a Haar field equals the
+    oracle's cooling sweep (the recipe of the cooled inputs)."""
+    dims = (4, 8, 4, 8)
+    U = synth.haar_field(dims, 31)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, links=U)
+    vs.vs_smooth_aus(f, 2, 1.0, 1.0, vortex_preserve=False)
+    Ug = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    assert max_abs(Ug, O.cool(dims, U, 2)) < 1e-12
+
+
+def test_aus_fp32_each_sweep_within_rounding(ctx):
+    dims = (8, 8, 8, 8)
+    lab = cooled_labels(dims, 2)
+    U = O.centrifuge(dims, lab, 0.02, 1234)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    worst = 0.0
+    for sweep in range(30):
+        vs.vs_load_field(f, links=U)
+        vs.vs_smooth_aus(f, 1, 0.02, -0.25, vortex_preserve=True, reunit_every=0)
+        Ug = vs.vs_read_field(f)
+        U, _ = O.aus(dims, U, lab, 1, 0.02, eps=-0.25, vp=True)
+        worst = max(worst, max_abs(Ug, U))
+    vs.vs_field_destroy(f)
+    assert worst < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Random gauge (Sec. V.D) with the gauge-reversed vortex-preservation test
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("method", ["stout", "aus"])
+def test_random_gauge_smoothing_matches_oracle(ctx, method):
+    """The VP recipe of the paper: centrifuge, random gauge transformation,
+    annealed smoothing with the vortex-preservation test applied to
+    G^dag(x) U' G(x+mu); FP64 against the oracle, identical reject counts,
+    and zero gauge-reversed label differences."""
+    dims = (8, 8, 8, 8)
+    lab = cooled_labels(dims, 2)
+    G = synth.random_gauge(dims, 41)
+    U0 = O.gauge_transform(dims, O.centrifuge(dims, lab, 0.02, 1234), G)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=lab)
+    vs.vs_centrifuge(f, 0.02, 1234)
+    vs.vs_gauge_transform(f, G)
+    assert max_abs(vs.vs_read_field(f), U0) < 1e-14
+    if method == "stout":
+        Uo, rej = O.smooth(dims, U0, lab, 6, 0.3, eps=-0.25, vp=True, gauge=G)
+        st = vs.vs_smooth(f, 6, 0.3, -0.25, vortex_preserve=True, stats=True)
+    else:
+        Uo, rej = O.aus(dims, U0, lab, 10, 0.02, eps=-0.25, vp=True, gauge=G)
+        st = vs.vs_smooth_aus(f, 10, 0.02, -0.25, vortex_preserve=True, stats=True)
+    Ug = vs.vs_read_field(f)
+    chk = vs.vs_vortex_check(f)
+    vs.vs_field_destroy(f)
+    assert [s["n_reject"] for s in st] == list(rej)
+    assert max_abs(Ug, Uo) < 1e-10
+    assert chk["n_label_diff"] == 0 and chk["n_charge_diff"] == 0
+    ref = O.vortex_check(dims, Uo, lab, gauge=G)
+    assert ref["n_label_diff"] == 0
+    if method == "stout":
+        assert rej.sum() > 0
+
+
+# --------------------------------------------------------------------------
+# Smoothness observables (Sec. V)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_observables_match_oracle(ctx, prec, tol):
+    """Clover F, S_R(x), q(x) and S(x) per site against the oracle, on a
+    smoothed centrifuged field and on the uniform two-plane flux field whose
+    q(x) is known in closed form."""
+    from tests.test_oracle_pins import _uniform_flux_field
+    p = vs.VS_FP64 if prec == "fp64" else vs.VS_FP32
+    dims = (8, 8, 4, 8)
+    lab = synth.iid_labels(dims, 21)
+    U = O.smooth(dims, O.centrifuge(dims, lab, 0.02, 1234), lab, 5, 0.06, eps=-0.25)[0]
+    Uf, (p1, p2) = _uniform_flux_field(dims, [(0, 1, 1), (2, 3, 1)])
+    for links in (U, Uf):
+        f = vs.vs_field_create(ctx, dims, p, vs.VS_LINK18)
+        vs.vs_load_field(f, links=links)
+        r = vs.vs_observables(f, per_site=True)
+        vs.vs_field_destroy(f)
+        SR, Q, SRs, qs = O.observables(dims, links, per_site=True)
+        S, Ss = O.action(dims, links, per_site=True)
+        assert np.abs(r["S_R"] - SRs).max() < tol
+        assert np.abs(r["q"] - qs).max() < tol
+        assert np.abs(r["S"] - Ss).max() < tol
+        assert abs(r["mean_SR"] - SR) < tol and abs(r["mean_S"] - S) < tol
+        assert abs(r["Q"] - Q) < tol * int(np.prod(dims))
+    assert abs(r["q"][0] - np.sin(p1) * np.sin(p2) / (2 * np.pi ** 2)) < tol
+    assert abs(vs.correlation(r["S"], r["S"]) - 1) < 1e-12

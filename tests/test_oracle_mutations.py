@@ -60,9 +60,25 @@ MUTATIONS = [
      "const pstep plaq[4] = {{mu, +1}, {nu, +1}, {nu, -1}, {mu, -1}};",
      pins.test_action_closed_forms, ()),
     ("vortex preservation against the current label",
-     "if (vp && label_of_trace(m_trace(&Un)) != ref_labels[li]) {",
-     "if (vp && label_of_trace(m_trace(&Un)) != label_of_trace(m_trace(&Ux))) {",
+     "if (vp && label_of_trace(tr) != ref_labels[li]) {",
+     "if (vp && label_of_trace(tr) != label_of_trace(m_trace(&Ux))) {",
      pins.test_vortex_preservation_keeps_original_labels, ()),
+    ("blocking weight of the staples",
+     "m_axpy(&Vb, alpha / 6.0, &S);",
+     "m_axpy(&Vb, alpha / 3.0, &S);",
+     pins.test_aus_below_alpha_min_leaves_vortex_fields_unchanged, ()),
+    ("vortex preservation ignores the random gauge",
+     "    if (!G) return m_trace(Un);",
+     "    return m_trace(Un);",
+     pins.test_vortex_preservation_in_random_gauge, ()),
+    ("clover leaf with the wrong orientation",
+     "{{nu, -1}, {mu, +1}, {nu, +1}, {mu, -1}}};",
+     "{{mu, +1}, {nu, -1}, {mu, -1}, {nu, +1}}};",
+     pins.test_topological_charge_density_on_two_plane_flux, ()),
+    ("reconstructed action without the 1/2",
+     "sr += 0.5 * creal(m_trace(&FF));",
+     "sr += creal(m_trace(&FF));",
+     pins.test_reconstructed_action_on_uniform_flux, ()),
     ("cooling subgroup conjugation",
      "Tc.m[p][q] = -be / k;",
      "Tc.m[p][q] = be / k;",

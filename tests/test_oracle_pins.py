@@ -607,3 +607,203 @@ def test_annealed_flow_amplifies_small_perturbations():
     b, _ = O.smooth(dims, U1, None, 40, 0.06, eps=-0.25, vp=False)
     assert np.abs(U1 - U0).max() < 2e-10
     assert np.abs(a - b).max() > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Annealed U-link smearing with MaxReTr (Sec. III, Sec. VI)
+# --------------------------------------------------------------------------
+
+def test_maxretr_never_lowers_re_tr():
+    """Each SU(2) subgroup hit maximises Re Tr(U V^dag) within its subgroup
+    (Eq. maxReTr), so the objective never decreases and the result is SU(3)."""
+    rng = np.random.default_rng(91)
+    Us = _rand_su3(50, 92)
+    for U in Us:
+        V = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        prev = np.real(np.trace(U @ L.dag(V)))
+        for hits in (1, 2, 3, 6):
+            W = O.maxretr(U, V, hits)
+            cur = np.real(np.trace(W @ L.dag(V)))
+            assert cur >= prev - 1e-12
+            prev = cur
+            assert np.abs(W @ L.dag(W) - np.eye(3)).max() < 1e-13
+            assert abs(np.linalg.det(W) - 1) < 1e-13
+
+
+def test_maxretr_on_vortex_links_follows_the_sign_of_r_cos_phi():
+    """Sec. III: on a vortex field L1 = r e^{i phi} I; if r cos(phi) > 0 every T^c
+    is the identity and the link is unchanged; otherwise it moves, and (Sec. VI,
+    p_pass = 0) the moved link never projects back to its own Z(3) element."""
+    dims = (8, 8, 8, 8)
+    lab = synth.iid_labels(dims, 3, p0=1 / 3, p_plus=1 / 3)
+    Z = O.links_from_labels(dims, lab)
+    c0, c1 = O.overimproved_coeffs(-0.25)
+    alpha = 0.7
+    seen = {True: 0, False: 0}
+    for s in range(0, 4096, 29):
+        x = np.unravel_index(s, dims[::-1])[::-1]
+        for mu in range(4):
+            S = O.staple_sum(dims, Z, mu, x, c0, c1)
+            Vb = (1 - alpha) * Z[mu, s] + alpha / 6 * S
+            w = (Z[mu, s] @ L.dag(Vb))[0, 0]          # L1 = w I
+            new = O.maxretr(Z[mu, s], Vb, 3)
+            stays = w.real > 0
+            seen[stays] += 1
+            if stays:
+                assert np.abs(new - Z[mu, s]).max() < 1e-14
+            else:
+                assert np.abs(new - Z[mu, s]).max() > 1e-3
+                assert O.label_matrix(new) != lab[mu, s]
+    assert seen[True] > 50 and seen[False] > 20
+
+
+def test_aus_below_alpha_min_leaves_vortex_fields_unchanged():
+    # Eq. alpha_condition_ape: no link combination gives r cos(phi) < 0 for
+    # alpha < alpha_min(-0.25, 1) = 0.4486
+    dims = (8, 8, 8, 8)
+    for p0 in (1 / 3, 0.7):
+        lab = synth.iid_labels(dims, 5, p0=p0, p_plus=(1 - p0) / 2)
+        Z = O.links_from_labels(dims, lab)
+        out, rej = O.aus(dims, Z, lab, 2, 0.44, eps=-0.25, vp=False)
+        assert np.abs(out - Z).max() < 1e-14
+
+
+def test_aus_moves_every_centrifuged_link_and_vp_passes_small_alpha():
+    # Sec. VI after centrifuge preconditioning: every updated link differs from
+    # the original at every alpha, and at small alpha every candidate passes
+    # the vortex-preservation test
+    dims = (8, 8, 8, 8)
+    lab = synth.iid_labels(dims, 3, p0=1 / 3, p_plus=1 / 3)
+    U0 = O.centrifuge(dims, lab, 0.02, 1234)
+    for alpha in (0.1, 0.5, 1.0):
+        out, _ = O.aus(dims, U0, lab, 1, alpha, eps=-0.25, vp=False)
+        assert np.all(np.abs(out - U0).max(axis=(2, 3)) > 1e-12)
+    for alpha in (0.02, 0.1, 0.3):
+        out, rej = O.aus(dims, U0, lab, 1, alpha, eps=-0.25, vp=True)
+        assert rej[0] == 0
+        assert np.array_equal(O.labels(dims, out), lab)
+
+
+def test_cooling_singularity_leaves_the_link():
+    # Sec. III.A: Sigma = 2 I + 4 e^{2 pi i/3} I = i 2 sqrt(3) I, Z = I, alpha = 1:
+    # T1 = 0 on its block, k = 0; the reading used keeps the link unchanged
+    S = (2 + 4 * np.exp(2j * np.pi / 3)) * np.eye(3)
+    new = O.maxretr(np.eye(3), S / 6, 3)
+    assert np.isfinite(new).all()
+    assert np.abs(new - np.eye(3)).max() < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Random gauge (Sec. V.D) and the gauge-reversed vortex-preservation test (Sec. VI)
+# --------------------------------------------------------------------------
+
+def test_vortex_preservation_in_random_gauge():
+    """After U -> G(x) U G^dag(x+mu), stout smoothing is gauge equivariant
+    (Sec. V.D), and the VP test on G^dag(x) U' G(x+mu) (Sec. VI) makes exactly
+    the decisions it makes in the original gauge: smoothing the transformed
+    field with the reversed test equals transforming the smoothed field."""
+    dims = (4, 4, 4, 8)
+    lab = synth.iid_labels(dims, 13)
+    U0 = O.centrifuge(dims, lab, 0.02, 1234)
+    G = synth.random_gauge(dims, 14)
+    a, ra = O.smooth(dims, U0, lab, 4, 0.5, eps=-0.25, vp=True)
+    assert ra.sum() > 0
+    b, rb = O.smooth(dims, O.gauge_transform(dims, U0, G), lab, 4, 0.5, eps=-0.25, vp=True, gauge=G)
+    assert list(ra) == list(rb)
+    # rounding of the gauge products differs between the two sides and is
+    # amplified by the large steps (rho = 0.5) over 4 sweeps
+    assert np.abs(O.gauge_transform(dims, a, G) - b).max() < 1e-9
+    # the gauge-reversed labels are the original ones; the plain labels are not
+    chk = O.vortex_check(dims, b, lab, gauge=G)
+    assert chk["n_label_diff"] == 0 and chk["n_charge_diff"] == 0
+    assert O.vortex_check(dims, b, lab)["n_label_diff"] > 0
+
+
+def test_aus_in_random_gauge_leaves_the_diagonal_subgroup():
+    """Sec. V.C-D: in MCG the smoothed centrifuged field stays diagonal; MaxReTr
+    in a random gauge is not gauge equivariant, and transformed back the
+    smoothed links are no longer diagonal."""
+    dims = (4, 4, 4, 8)
+    lab = synth.iid_labels(dims, 15)
+    U0 = O.centrifuge(dims, lab, 0.02, 1234)
+    a, _ = O.aus(dims, U0, lab, 3, 0.1, eps=-0.25, vp=False)
+    off = a.copy()
+    for k in range(3):
+        off[..., k, k] = 0
+    assert np.abs(off).max() < 1e-15
+    G = synth.random_gauge(dims, 16)
+    b, _ = O.aus(dims, O.gauge_transform(dims, U0, G), lab, 3, 0.1, eps=-0.25, vp=False, gauge=G)
+    Gi = np.conj(np.swapaxes(G, -1, -2))
+    back = O.gauge_transform(dims, b, Gi)
+    off = back.copy()
+    for k in range(3):
+        off[..., k, k] = 0
+    assert np.abs(off).max() > 1e-5           # far above rounding (1e-15 in MCG)
+
+
+# --------------------------------------------------------------------------
+# Smoothness observables (Sec. V): clover F, reconstructed action, q(x)
+# --------------------------------------------------------------------------
+
+def _uniform_flux_field(dims, planes):
+    """Abelian field with the same plaquette angle phi in each given plane (mu, nu, k):
+    phi = 2 pi k / (L_mu L_nu), generator T = diag(1, -1, 0).  U_nu(x) =
+    exp(i phi x_mu T), and U_mu carries the twist exp(-i phi L_mu x_nu T) on the
+    last mu-slice, so every plaquette of the plane is exp(i phi T)."""
+    V = int(np.prod(dims))
+    ang = np.zeros((4, V))
+    coords = np.array(np.unravel_index(np.arange(V), dims[::-1])[::-1])
+    phis = []
+    for mu, nu, k in planes:
+        phi = 2 * np.pi * k / (dims[mu] * dims[nu])
+        phis.append(phi)
+        ang[nu] += phi * coords[mu]
+        ang[mu] -= np.where(coords[mu] == dims[mu] - 1, phi * dims[mu] * coords[nu], 0.0)
+    U = np.zeros((4, V, 3, 3), dtype=np.complex128)
+    U[:, :, 0, 0] = np.exp(1j * ang)
+    U[:, :, 1, 1] = np.exp(-1j * ang)
+    U[:, :, 2, 2] = 1.0
+    return U, phis
+
+
+def test_reconstructed_action_on_uniform_flux():
+    """One plane of uniform flux phi: every leaf equals exp(i phi T), so
+    S/beta = 4 (1 - cos phi)/72 and S_R/beta = 2 sin^2(phi)/72 per site:
+    S_R / S = (1 + cos phi)/2 -> 1 on smooth fields; q = 0."""
+    dims = (8, 8, 4, 4)
+    for k in (1, 3):
+        U, (phi,) = _uniform_flux_field(dims, [(0, 1, k)])
+        S = O.action(dims, U)
+        SR, Q = O.observables(dims, U)
+        assert abs(S - 4 * (1 - np.cos(phi)) / 72) < 1e-14
+        assert abs(SR - 2 * np.sin(phi) ** 2 / 72) < 1e-14
+        assert abs(SR / S - (1 + np.cos(phi)) / 2) < 1e-12
+        assert abs(Q) < 1e-12
+
+
+def test_topological_charge_density_on_two_plane_flux():
+    """Flux phi1 in (0,1) and phi2 in (2,3): F_01 = sin(phi1 T), F_23 = sin(phi2 T),
+    so q(x) = 8 Tr(F_01 F_23) / (32 pi^2) = sin(phi1) sin(phi2) / (2 pi^2) at every
+    site (Eq. 1LTopQ); reversing one flux reverses q."""
+    dims = (4, 8, 4, 8)
+    V = int(np.prod(dims))
+    U, (p1, p2) = _uniform_flux_field(dims, [(0, 1, 1), (2, 3, 2)])
+    SR, Q, SRs, qs = O.observables(dims, U, per_site=True)
+    ref = np.sin(p1) * np.sin(p2) / (2 * np.pi ** 2)
+    assert np.abs(qs - ref).max() < 1e-15
+    assert abs(Q - V * ref) < 1e-11
+    Um, _ = _uniform_flux_field(dims, [(0, 1, 1), (2, 3, -2)])
+    assert abs(O.observables(dims, Um)[1] + Q) < 1e-11
+
+
+def test_observables_are_gauge_invariant_and_vanish_on_pure_gauge():
+    dims = (4, 4, 4, 8)
+    U = O.cool(dims, synth.haar_field(dims, 61), 2)
+    G = synth.random_gauge(dims, 62)
+    a = O.observables(dims, U, per_site=True)
+    b = O.observables(dims, O.gauge_transform(dims, U, G), per_site=True)
+    assert np.abs(a[2] - b[2]).max() < 1e-13 and np.abs(a[3] - b[3]).max() < 1e-13
+    I = np.broadcast_to(np.eye(3), U.shape).astype(np.complex128)
+    pg = O.gauge_transform(dims, I, G)
+    SR, Q = O.observables(dims, pg)
+    assert abs(SR) < 1e-13 and abs(Q) < 1e-13
