@@ -40,7 +40,7 @@ BYTES_PER_UPDATE = {(1, 18): 17 * 72 + 1, (1, 12): 17 * 48 + 1, (0, 18): 17 * 14
 FLOPS_PER_UPDATE_OVERIMPROVED = 65 * 216 + 600
 # DRAM bytes (read + write) of one class-update launch of this kernel version,
 # from `ncu --set full` on the same command (profiles/k_subsweep_f32_*.md)
-NCU_TRAFFIC_PER_LAUNCH = 937.392384e6 + 54.278144e6
+NCU_TRAFFIC_PER_LAUNCH = 932.4032e6 + 49.73568e6
 
 
 def _env_int(k, d):
