@@ -39,8 +39,10 @@ REUNIT = 10
 BYTES_PER_UPDATE = {(1, 18): 17 * 72 + 1, (1, 12): 17 * 48 + 1, (0, 18): 17 * 144 + 1}
 FLOPS_PER_UPDATE_OVERIMPROVED = 65 * 216 + 600
 # DRAM bytes (read + write) of one class-update launch of this kernel version,
-# from `ncu --set full` on the same command (profiles/k_subsweep_f32_*.md)
-NCU_TRAFFIC_PER_LAUNCH = 932.4032e6 + 49.73568e6
+# from `ncu --set full` on the same command (profiles/k_subsweep_ring_f32_*.md)
+NCU_TRAFFIC_PER_LAUNCH = 722.3808e6 + 36.041216e6
+# FP32 FMA peak of the GPU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _env_int(k, d):
@@ -250,13 +252,14 @@ def run_ours(args):
     units = V // 4
     bpu = BYTES_PER_UPDATE[(1, 18)]
     achieved = units * bpu / (per_launch_ms / 1e3) / 1e9
-    line["roofline"] = {"kernel": "k_subsweep<float,18,rect>", "bound": "hbm",
+    tflops = units * FLOPS_PER_UPDATE_OVERIMPROVED / (per_launch_ms / 1e3) / 1e12
+    line["roofline"] = {"kernel": "k_subsweep_ring<18,mu> (FP32 over-improved class update)", "bound": "hbm",
                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_PER_LAUNCH,
                         "peak_source": src, "per_launch_ms": per_launch_ms,
                         "bytes_per_update": bpu, "updates_per_launch": units,
-                        "achieved_tflops": units * FLOPS_PER_UPDATE_OVERIMPROVED
-                        / (per_launch_ms / 1e3) / 1e12}
+                        "achieved_tflops": tflops, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
+                        "fp32_frac": tflops / FP32_PEAK_TFLOPS}
 
     # ---- the same step with 12-real links (rows 1-2 stored, row 3 rebuilt) ----
     if not args.no_fp64:

@@ -130,12 +130,77 @@ __device__ __forceinline__ M3<T> m3_dag(const M3<T> &a) {
     return r;
 }
 
-// r = a * b.  Every entry is the same chain of fused multiply-adds started
-// from zero, so entries built from equal inputs come out bit-identical (a
-// product of matrices proportional to the identity stays exactly so).
+// FP32 complex entries as packed pairs (re, im) for the paired FP32 FMA of
+// sm_100 and later (fma.rn.f32x2: two independent FMAs in one instruction).
+// VS_FFMA2=0 selects the scalar FMA chains for FP32 as well.
+#ifndef VS_FFMA2
+#define VS_FFMA2 1
+#endif
+typedef unsigned long long f2pk;
+__device__ __forceinline__ f2pk pk2(float lo, float hi) {
+    f2pk r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2pk v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2pk fma2(f2pk a, f2pk b, f2pk c) {
+    f2pk d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// r = c + a * b in FP32: per entry, P = (Re c, Im c) + sum_k Re a_ik (Re b_kj, Im b_kj)
+// and Q = sum_k Im a_ik (Re b_kj, Im b_kj), each a chain of paired FMAs in k
+// order, then r_ij = (P.re - Q.im, P.im + Q.re).  Every entry goes through
+// the same operations, so entries built from equal inputs come out
+// bit-identical (a product of matrices proportional to the identity stays
+// exactly so).
+template <bool ACC>
+__device__ __forceinline__ void m3_mul_f32(M3<float> &r, const M3<float> &a, const M3<float> &b) {
+    f2pk bb[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) bb[e] = pk2(b.re[e], b.im[e]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        f2pk P[3], Q[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            P[j] = ACC ? pk2(r.re[i * 3 + j], r.im[i * 3 + j]) : pk2(0.f, 0.f);
+            Q[j] = pk2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const f2pk ar = pk2(a.re[i * 3 + k], a.re[i * 3 + k]);
+            const f2pk ai = pk2(a.im[i * 3 + k], a.im[i * 3 + k]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                P[j] = fma2(ar, bb[k * 3 + j], P[j]);
+                Q[j] = fma2(ai, bb[k * 3 + j], Q[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float px, py, qx, qy;
+            upk2(P[j], px, py);
+            upk2(Q[j], qx, qy);
+            r.re[i * 3 + j] = px - qy;
+            r.im[i * 3 + j] = py + qx;
+        }
+    }
+}
+
+// r = a * b.  FP64: every entry is the same chain of fused multiply-adds
+// started from zero; FP32: m3_mul_f32.  Either way entries built from equal
+// inputs come out bit-identical.
 template <class T>
 __device__ __forceinline__ M3<T> m3_mul(const M3<T> &a, const M3<T> &b) {
     M3<T> r;
+    if constexpr (sizeof(T) == 4 && VS_FFMA2) {
+        m3_mul_f32<false>(r, a, b);
+        return r;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -157,6 +222,10 @@ __device__ __forceinline__ M3<T> m3_mul(const M3<T> &a, const M3<T> &b) {
 // r += a * b
 template <class T>
 __device__ __forceinline__ void m3_madd(M3<T> &r, const M3<T> &a, const M3<T> &b) {
+    if constexpr (sizeof(T) == 4 && VS_FFMA2) {
+        m3_mul_f32<true>(r, a, b);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll

@@ -236,6 +236,14 @@ __device__ __forceinline__ bool ch_exp_coeffs(R h00, R h11, R h22, R h01r, R h01
     return r2 <= rmax * rmax;
 }
 
+// FP64 redo of the coefficients for FP32 kernels (|H|_F > 1), out of line:
+// the workloads never take it, and inlined it would put ~37 KB of cold code
+// between the hot parts of the class-update kernel.
+static __device__ __noinline__ void ch_exp_coeffs_fp64(double h00, double h11, double h22, double h01r, double h01i,
+                                                double h02r, double h02i, double h12r, double h12i, double fd[6]) {
+    ch_exp_coeffs<double, 12>(h00, h11, h22, h01r, h01i, h02r, h02i, h12r, h12i, 1e300, fd);
+}
+
 // M = exp(i H) for Hermitian traceless H given by its diagonal and upper
 // entries.  fp64_used reports an FP64 redo of the coefficients.
 template <class T>
@@ -248,7 +256,7 @@ __device__ __forceinline__ M3<T> exp_iH(T h00, T h11, T h22, T h01r, T h01i, T h
         // coefficients are redone in FP64 (48 terms, accurate to |H|_F <= 8).
         if (!ch_exp_coeffs<T, 3>(h00, h11, h22, h01r, h01i, h02r, h02i, h12r, h12i, T(1.0), f)) {
             double fd[6];
-            ch_exp_coeffs<double, 12>(h00, h11, h22, h01r, h01i, h02r, h02i, h12r, h12i, 1e300, fd);
+            ch_exp_coeffs_fp64(h00, h11, h22, h01r, h01i, h02r, h02i, h12r, h12i, fd);
 #pragma unroll
             for (int k = 0; k < 6; ++k) f[k] = T(fd[k]);
             fp64_used = true;
@@ -301,6 +309,37 @@ __device__ __forceinline__ M3<T> stout_candidate(const M3<T> &sig, const M3<T> &
 #define VS_SUBSWEEP_MINB (512 / VS_SUBSWEEP_THREADS)
 #endif
 
+// Stout candidate for link (x, MU) at plane position i from its staple sum,
+// vortex-preservation test against the reference label, store if accepted.
+template <class T, int NC, int MU>
+__device__ __forceinline__ void stout_store(const SubsweepParams &a, const Pt &x, int i, const M3<T> &sig,
+                                            const M3<T> &Ux, bool &reject, bool &used64) {
+    const Geo &g = a.g;
+    const T rho = sizeof(T) == 4 ? T(a.rho_f) : T(a.rho);
+    M3<T> Un = stout_candidate<T>(sig, Ux, rho, used64);
+    // 12-real storage keeps rows 0-1 and rebuilds row 2 on every load: the
+    // test must see that matrix, not the one computed here
+    if (NC == 12) rebuild_row2(Un);
+    if (a.vp) {
+        T tr_re, tr_im;
+        vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re, tr_im);
+        reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
+    }
+    if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Un);
+}
+
+// per-warp reject and FP64-exponential counts
+__device__ __forceinline__ void count_update(const SubsweepParams &a, bool reject, bool used64) {
+    if (a.counters) {
+        unsigned rb = __ballot_sync(0xffffffffu, reject);
+        unsigned fb = __ballot_sync(0xffffffffu, used64);
+        if ((threadIdx.x & 31) == 0) {
+            if (rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
+            if (fb) atomicAdd(&a.counters[1], (unsigned long long)__popc(fb));
+        }
+    }
+}
+
 // One thread per link of the colour class (or of direction MU when colour < 0).
 // FP32: at most 65536 / (VS_SUBSWEEP_THREADS * VS_SUBSWEEP_MINB) registers per
 // thread (128 by default), so VS_SUBSWEEP_MINB blocks fit on an SM (16 warps).
@@ -316,28 +355,312 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
         const int i = sidx(g, x);
         const T *Us = static_cast<const T *>(a.Usrc);
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
-        const T rho = sizeof(T) == 4 ? T(a.rho_f) : T(a.rho);
         M3<T> sig = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
         M3<T> Ux = load_link<T, NC>(Us, g.P, MU, i);
-        M3<T> Un = stout_candidate<T>(sig, Ux, rho, used64);
-        // 12-real storage keeps rows 0-1 and rebuilds row 2 on every load: the
-        // test must see that matrix, not the one computed here
-        if (NC == 12) rebuild_row2(Un);
-        if (a.vp) {
-            T tr_re, tr_im;
-            vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re, tr_im);
-            reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
-        }
-        if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Un);
+        stout_store<T, NC, MU>(a, x, i, sig, Ux, reject, used64);
     }
-    if (a.counters) {
-        unsigned rb = __ballot_sync(0xffffffffu, reject);
-        unsigned fb = __ballot_sync(0xffffffffu, used64);
-        if ((threadIdx.x & 31) == 0) {
-            if (rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
-            if (fb) atomicAdd(&a.counters[1], (unsigned long long)__popc(fb));
+    count_update(a, reject, used64);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 over-improved update with the link loads running ahead of the
+// arithmetic.  Each thread keeps the next kRingDepth links it will read in
+// flight as asynchronous global -> shared copies (cp.async) into its own ring
+// of slots, so no register holds a pending load and the latency of one link
+// is covered by the products of the kRingDepth - 1 before it.  A slot is
+// refilled with the link kRingDepth places ahead right after it is read.
+//
+// The wide backward rectangles of link (x, mu) are the wide forward ones of
+// the site below: -mu +nu +mu +mu -nu from x is the path +nu +mu +mu -nu
+// from x - mu, closed by U_mu^dag(x - mu) on the left instead of
+// U_mu^dag(x + mu) on the right.  So with
+//   F(y) = sum_{nu, s} step(y, s nu) U_mu(y + s nu) U_mu(y + s nu + mu) step(y + s nu + 2 mu, -s nu)
+// the rectangle part of Sigma is c1 [F(x) U_mu^dag(x+mu) + U_mu^dag(x-mu) F(x-mu)]
+// and one code body, run with anchor x and x - mu, serves both (each chain
+// multiplied left to right).  Then staples and tall rectangles as in
+// staple_sum.  The 84 + 1 ring links, in order:
+//   F(x), F(x - mu): 4 links per (nu, s), s = +1 then -1, nu = MU+1, MU+2, MU+3
+//   staples + tall:  6 links per (nu, s)
+//   U_mu(x)
+// U_mu(x +- mu) are read with plain loads, one pass ahead of their use.
+// ---------------------------------------------------------------------------
+
+#ifndef VS_RING
+#define VS_RING 1
+#endif
+#ifndef VS_RING_THREADS
+#define VS_RING_THREADS 128
+#endif
+#ifndef VS_RING_MINB
+#define VS_RING_MINB (384 / VS_RING_THREADS)
+#endif
+
+constexpr int kRingDepth = 4;   // the stream patterns below assume 4
+
+template <int NC>
+struct LinkRing {
+    const float4 *v4;   // this thread's column of the float4 slots [kRingDepth][NC/4][BT]
+    const float2 *v2;   // and of the float2 slots [kRingDepth][BT] (NC == 18)
+    uint32_t a4, a2;    // the same as shared-window addresses
+};
+
+// Start the copy of the link at plane position i of the direction whose
+// planes begin at base into slot SLOT, as one commit group.
+template <int NC, int SLOT>
+__device__ __forceinline__ void ring_fetch(const LinkRing<NC> &R, const float *base, long long P, int i) {
+    constexpr int NQ = NC / 4;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float4 *src = reinterpret_cast<const float4 *>(base + 4 * q * P) + i;
+        const uint32_t dst = R.a4 + (uint32_t)((SLOT * NQ + q) * VS_RING_THREADS * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    if (NC == 18) {
+        const float2 *src = reinterpret_cast<const float2 *>(base + 16 * P) + i;
+        const uint32_t dst = R.a2 + (uint32_t)(SLOT * VS_RING_THREADS * 8);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Past the end of the stream: an empty group keeps one group per link.
+__device__ __forceinline__ void ring_skip() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Wait for the link in slot SLOT (all but the kRingDepth - 1 newest groups
+// are complete) and read it, daggered if DAG.
+template <int NC, bool DAG, int SLOT>
+__device__ __forceinline__ M3<float> ring_take(const LinkRing<NC> &R) {
+    constexpr int NQ = NC / 4;
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRingDepth - 1) : "memory");
+    M3<float> m;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float4 v = R.v4[(SLOT * NQ + q) * VS_RING_THREADS];
+        m.re[2 * q] = v.x; m.im[2 * q] = v.y; m.re[2 * q + 1] = v.z; m.im[2 * q + 1] = v.w;
+    }
+    if (NC == 18) {
+        const float2 v = R.v2[SLOT * VS_RING_THREADS];
+        m.re[8] = v.x; m.im[8] = v.y;
+    }
+    if (NC == 12) rebuild_row2(m);
+    return DAG ? m3_dag(m) : m;
+}
+
+// Plane-position shifts along mu of the anchor of F: b0, b1, b2 are the
+// shifts to anchor + 0, 1, 2 mu (anchor x: 0, D(1), D(2); anchor x - mu:
+// D(-1), 0, D(1)).
+struct MuOff { int b0, b1, b2; };
+
+// Link K of an F unit (nu, s): K0 = step(y, s nu), K1 = U_mu(y + s nu),
+// K2 = U_mu(y + s nu + mu), K3 = step(y + s nu + 2 mu, -s nu).  A nu-link
+// stepped backwards sits one site further down: the nu offset of the step
+// that starts at y is 0 for s = +1 and -1 for s = -1.
+template <int S, int K>
+__device__ __forceinline__ void f_link(const Around &A, const MuOff &m, const float *Umu, const float *Unu,
+                                       const float *&base, int &pos) {
+    constexpr int a = (K == 0 || K == 3) ? (S > 0 ? 0 : -1) : S;
+    const int dn = around_pos(A, a, 0) - A.i0;
+    const int db = K == 0 || K == 1 ? m.b0 : K == 2 ? m.b1 : m.b2;
+    base = (K == 1 || K == 2) ? Umu : Unu;
+    pos = A.i0 + dn + db;
+}
+
+// Link K of a staple + tall unit (nu, s): K0 = step(x + s nu, s nu),
+// K1 = U_mu(x + 2 s nu), K2 = step(x + 2 s nu + mu, -s nu), K3 = U_mu(x + s nu),
+// K4 = step(x, s nu), K5 = step(x + s nu + mu, -s nu).
+template <int S, int K>
+__device__ __forceinline__ void t_link(const Around &A, const float *Umu, const float *Unu, const float *&base,
+                                       int &pos) {
+    constexpr int a = (K == 0 || K == 2) ? (S > 0 ? 1 : -2) : K == 1 ? 2 * S : K == 3 ? S : (S > 0 ? 0 : -1);
+    constexpr int b = (K == 2 || K == 5) ? 1 : 0;
+    base = (K == 1 || K == 3) ? Umu : Unu;
+    pos = around_pos(A, a, b);
+}
+
+// Stream slots: F units start at multiples of 4; staple units at 48 + 6u.
+template <int S, int K> struct TSlot { static constexpr int v = ((S < 0 ? 2 : 0) + K) & 3; };
+
+// Refill after link K of F unit (nu, s): link K of the next unit, which is
+// (nu, -s) for s = +1; for s = -1 the next nu (An), or after the last nu the
+// first unit of F(x - mu) (mnext) or, after F(x - mu), the first staple unit.
+// The candidates are selected, not branched to.
+template <int NC, int S, int K>
+__device__ __forceinline__ void f_refill(const LinkRing<NC> &R, const float *Umu, const float *Unu,
+                                         const float *Un, long long P, const Around &A, const Around &An,
+                                         const MuOff &m, const MuOff &mnext, bool to_staples) {
+    const float *base;
+    int pos;
+    if constexpr (S > 0) {
+        f_link<-1, K>(A, m, Umu, Unu, base, pos);
+    } else {
+        const float *bt;
+        int pt;
+        f_link<1, K>(An, mnext, Umu, Un, base, pos);
+        t_link<1, K>(An, Umu, Un, bt, pt);
+        base = to_staples ? bt : base;
+        pos = to_staples ? pt : pos;
+    }
+    ring_fetch<NC, K>(R, base, P, pos);
+}
+
+// F += step(y, s nu) U_mu(y + s nu) U_mu(y + s nu + mu) step(y + s nu + 2 mu, -s nu)
+template <int NC, int S>
+__device__ __forceinline__ void f_unit(const LinkRing<NC> &R, M3<float> &F, const float *Umu, const float *Unu,
+                                       const float *Un, long long P, const Around &A, const Around &An,
+                                       const MuOff &m, const MuOff &mnext, bool to_staples) {
+    M3<float> L0 = ring_take<NC, (S < 0), 0>(R);
+    f_refill<NC, S, 0>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+    M3<float> L1 = ring_take<NC, false, 1>(R);
+    f_refill<NC, S, 1>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+    M3<float> W = m3_mul(L0, L1);
+    M3<float> L2 = ring_take<NC, false, 2>(R);
+    f_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+    W = m3_mul(W, L2);
+    M3<float> L3 = ring_take<NC, (S > 0), 3>(R);
+    f_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+    m3_madd(F, W, L3);
+}
+
+// Refill after link K of staple unit (nu, s): 4 places ahead in units of 6.
+template <int NC, int S, int K>
+__device__ __forceinline__ void t_refill(const LinkRing<NC> &R, const float *Umu, const float *Unu,
+                                         const float *Un, long long P, const Around &A, const Around &An,
+                                         bool last) {
+    constexpr int SL = TSlot<S, K>::v;
+    const float *base;
+    int pos;
+    if constexpr (K <= 1) {
+        t_link<S, K + 4>(A, Umu, Unu, base, pos);
+        ring_fetch<NC, SL>(R, base, P, pos);
+    } else if constexpr (S > 0) {
+        t_link<-1, K - 2>(A, Umu, Unu, base, pos);
+        ring_fetch<NC, SL>(R, base, P, pos);
+    } else if constexpr (K == 2) {
+        // next nu, or U_mu(x) after the last
+        t_link<1, 0>(An, Umu, Un, base, pos);
+        ring_fetch<NC, SL>(R, last ? Umu : base, P, last ? A.i0 : pos);
+    } else {
+        if (last) {
+            ring_skip();
+        } else {
+            t_link<1, K - 2>(An, Umu, Un, base, pos);
+            ring_fetch<NC, SL>(R, base, P, pos);
         }
     }
+}
+
+// Sigma += step(x, s nu) (c0 U_mu(x + s nu) + c1 T) step(x + s nu + mu, -s nu),
+// T = step(x + s nu, s nu) U_mu(x + 2 s nu) step(x + 2 s nu + mu, -s nu)
+template <int NC, int S>
+__device__ __forceinline__ void t_unit(const LinkRing<NC> &R, M3<float> &sig, float c0, float c1,
+                                       const float *Umu, const float *Unu, const float *Un, long long P,
+                                       const Around &A, const Around &An, bool last) {
+    M3<float> T0 = ring_take<NC, (S < 0), TSlot<S, 0>::v>(R);
+    t_refill<NC, S, 0>(R, Umu, Unu, Un, P, A, An, last);
+    M3<float> T1 = ring_take<NC, false, TSlot<S, 1>::v>(R);
+    t_refill<NC, S, 1>(R, Umu, Unu, Un, P, A, An, last);
+    M3<float> Tt = m3_mul(T0, T1);
+    M3<float> T2 = ring_take<NC, (S > 0), TSlot<S, 2>::v>(R);
+    t_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
+    Tt = m3_mul(Tt, T2);
+    M3<float> N = ring_take<NC, false, TSlot<S, 3>::v>(R);
+    t_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, last);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        N.re[k] = fmaf(c1, Tt.re[k], c0 * N.re[k]);
+        N.im[k] = fmaf(c1, Tt.im[k], c0 * N.im[k]);
+    }
+    M3<float> Af = ring_take<NC, (S < 0), TSlot<S, 4>::v>(R);
+    t_refill<NC, S, 4>(R, Umu, Unu, Un, P, A, An, last);
+    M3<float> AN = m3_mul(Af, N);
+    M3<float> C = ring_take<NC, (S > 0), TSlot<S, 5>::v>(R);
+    t_refill<NC, S, 5>(R, Umu, Unu, Un, P, A, An, last);
+    m3_madd(sig, AN, C);
+}
+
+// Sigma_mu(x) (over-improved, Eq. over-improvement) and U_mu(x) in Ux.
+template <int NC, int MU>
+__device__ __forceinline__ M3<float> staple_sum_ring(const Geo &g, const float *__restrict__ U, Pt x, float c0,
+                                                     float c1, const LinkRing<NC> &R, M3<float> &Ux) {
+    const long long P = g.P;
+    Around A, An;
+    A.i0 = sidx(g, x);
+    A.dmm1 = shift_delta(g, x, MU, -1);
+    A.dmp1 = shift_delta(g, x, MU, 1);
+    A.dmp2 = shift_delta(g, x, MU, 2);
+    An = A;
+    const MuOff m_x = {0, A.dmp1, A.dmp2}, m_xm = {A.dmm1, 0, A.dmp1};
+    const float *Umu = U + (long long)MU * NC * P;
+    const int nu1 = (MU + 1) & 3;
+    around_nu(g, x, nu1, true, A);
+    const float *Unu = U + (long long)nu1 * NC * P;
+    {   // prologue: the first unit of F(x) into slots 0-3
+        const float *b;
+        int q;
+        f_link<1, 0>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 0>(R, b, P, q);
+        f_link<1, 1>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 1>(R, b, P, q);
+        f_link<1, 2>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 2>(R, b, P, q);
+        f_link<1, 3>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 3>(R, b, P, q);
+    }
+    M3<float> sig;
+    m3_zero(sig);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        // h = 0: c1 F(x) U_mu^dag(x+mu);  h = 1: c1 U_mu^dag(x-mu) F(x-mu)
+        const MuOff m = h ? m_xm : m_x;
+        const M3<float> Lc = load_link<float, NC>(U, P, MU, A.i0 + (h ? A.dmm1 : A.dmp1));
+        M3<float> F;
+        m3_zero(F);
+#pragma unroll 1
+        for (int j = 1; j < 4; ++j) {
+            const bool last = j == 3;
+            const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
+            around_nu(g, x, nun, true, An);
+            const float *Un = U + (long long)nun * NC * P;
+            const MuOff mn = last ? m_xm : m;
+            f_unit<NC, 1>(R, F, Umu, Unu, Un, P, A, An, m, mn, last && h == 1);
+            f_unit<NC, -1>(R, F, Umu, Unu, Un, P, A, An, m, mn, last && h == 1);
+            A = An;
+            Unu = Un;
+        }
+        M3<float> t = h ? m3_mul_dn(Lc, F) : m3_mul_nd(F, Lc);
+        m3_axpy(sig, c1, t);
+    }
+#pragma unroll 1
+    for (int j = 1; j < 4; ++j) {
+        const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
+        around_nu(g, x, nun, true, An);
+        const float *Un = U + (long long)nun * NC * P;
+        t_unit<NC, 1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
+        t_unit<NC, -1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
+        A = An;
+        Unu = Un;
+    }
+    Ux = ring_take<NC, false, 0>(R);
+    return sig;
+}
+
+template <int NC, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring(SubsweepParams a) {
+    __shared__ float4 ring4[kRingDepth * (NC / 4) * VS_RING_THREADS];
+    __shared__ float2 ring2[NC == 18 ? kRingDepth * VS_RING_THREADS : 1];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false, used64 = false;
+    if (active) {
+        const Geo &g = a.g;
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        const int i = sidx(g, x);
+        LinkRing<NC> R;
+        R.v4 = ring4 + threadIdx.x;
+        R.v2 = ring2 + (NC == 18 ? threadIdx.x : 0);
+        R.a4 = (uint32_t)__cvta_generic_to_shared(ring4 + threadIdx.x);
+        R.a2 = (uint32_t)__cvta_generic_to_shared(ring2 + (NC == 18 ? threadIdx.x : 0));
+        M3<float> Ux;
+        M3<float> sig = staple_sum_ring<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
+        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
+    }
+    count_update(a, reject, used64);
 }
 
 }  // namespace vs
