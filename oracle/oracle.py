@@ -15,7 +15,7 @@ __all__ = [
     "label_matrix", "labels", "links_from_labels", "splitmix64", "centrifuge_pair",
     "centrifuge", "overimproved_coeffs", "staple_sum", "expm", "stout_generator",
     "colour", "smooth", "action", "centre_charges", "vortex_check", "gauge_transform",
-    "cool", "aus", "maxretr", "observables", "ANNEALED", "SIMULTANEOUS",
+    "cool", "aus", "maxretr", "observables", "ucp", "ape_ucp", "flow_rk3", "ANNEALED", "SIMULTANEOUS",
 ]
 
 ANNEALED = 0
@@ -114,6 +114,10 @@ def _declare(L):
                                   P, ctypes.c_int, P]),
         "or_maxretr": (ctypes.c_int, [P, P, ctypes.c_int, P]),
         "or_observables": (ctypes.c_int, [P, P, P, P, P, P]),
+        "or_ucp": (ctypes.c_int, [P, P]),
+        "or_ape_ucp": (ctypes.c_int, [P, P, P, ctypes.c_int, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                      P, ctypes.c_int, P]),
+        "or_flow_rk3": (ctypes.c_int, [P, P, ctypes.c_int, dbl, dbl, dbl, ctypes.c_int]),
         "or_max_threads": (ctypes.c_int, []),
     }
     for name, (res, args) in sig.items():
@@ -323,6 +327,41 @@ def maxretr(U, V, n_hits=3):
     out = np.empty((3, 3), dtype=np.complex128)
     _check(lib().or_maxretr(_p(Uc), _p(Vc), n_hits, _p(out)), "maxretr")
     return out
+
+
+def ucp(V):
+    """Unit circle projection of one matrix (Sec. II.C); None if V is singular."""
+    Vc = _c128(V, (3, 3))
+    out = np.empty((3, 3), dtype=np.complex128)
+    rc = lib().or_ucp(_p(Vc), _p(out))
+    return None if rc == 1 else out
+
+
+def ape_ucp(dims, links, ref_labels, n_sweeps, alpha, eps=1.0, u0=1.0, schedule="annealed", vp=True,
+            nthreads=None, gauge=None):
+    """n_sweeps of APE blocking with unit circle projection: schedule "annealed"
+    (AUS+UCP) or "simultaneous" (APE smearing); returns (links, n_reject)."""
+    d = _dims(dims)
+    U = np.array(links, dtype=np.complex128, order="C", copy=True)
+    ref = None if ref_labels is None else np.ascontiguousarray(ref_labels, dtype=np.int8)
+    rej = np.zeros(max(n_sweeps, 1), dtype=np.int64)
+    nt = max_threads() if nthreads is None else int(nthreads)
+    G = None if gauge is None else _c128(gauge)
+    sched = {"annealed": 0, "simultaneous": 1}[schedule]
+    _check(lib().or_ape_ucp(_p(d), _p(U), _p(ref) if ref is not None else None, n_sweeps, alpha, eps,
+                            u0, sched, 1 if vp else 0, _p(rej), nt, _p(G) if G is not None else None),
+           "ape_ucp")
+    return U, rej[:n_sweeps]
+
+
+def flow_rk3(dims, links, n_steps, h, eps=1.0, u0=1.0, nthreads=None):
+    """n_steps of the Wilson flow (staples Sigma(eps, u0)) by third-order
+    Runge-Kutta with step h; returns the links."""
+    d = _dims(dims)
+    U = np.array(links, dtype=np.complex128, order="C", copy=True)
+    nt = max_threads() if nthreads is None else int(nthreads)
+    _check(lib().or_flow_rk3(_p(d), _p(U), n_steps, h, eps, u0, nt), "flow_rk3")
+    return U
 
 
 def observables(dims, links, per_site=False):

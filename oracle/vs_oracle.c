@@ -841,6 +841,254 @@ int or_maxretr(const double *U18, const double *V18, int n_hits, double *out18) 
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Unit circle projection (Sec. II.C, Eqs. W and P_ucp)                       */
+/* ------------------------------------------------------------------------ */
+
+/* Eigen-decomposition A = E diag(lam) E^dag of a 3x3 Hermitian matrix by
+ * cyclic Jacobi rotations.  For the pair (p,q) with A_pq = |b| e^{i phi},
+ * the diagonal unitary that multiplies column q by e^{-i phi} makes the
+ * (p,q) entry real; the real plane rotation by theta, tan 2 theta =
+ * 2 |b| / (A_qq - A_pp), then zeroes it.  Sweeps repeat until the squared
+ * off-diagonal norm is below 1e-30 of the squared diagonal norm (rounding
+ * level: the off-diagonal part then changes the eigenvalues by ~1e-30). */
+static void herm_eig(const mat3 *A0, double lam[3], mat3 *E) {
+    mat3 A = *A0;
+    *E = m_eye();
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double a2 = creal(A.m[i][j] * conj(A.m[i][j]));
+                if (i == j) dia += a2; else off += a2;
+            }
+        if (off <= 1e-30 * dia) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                double b = cabs(A.m[p][q]);
+                if (b == 0.0) continue;
+                cplx ph = A.m[p][q] / b;                 /* e^{i phi} */
+                double th = 0.5 * atan2(2.0 * b, creal(A.m[q][q]) - creal(A.m[p][p]));
+                double c = cos(th), sn = sin(th);
+                /* J = D R with D = diag(1 at p, conj(ph) at q), R the rotation */
+                mat3 J = m_eye();
+                J.m[p][p] = c;
+                J.m[p][q] = sn;
+                J.m[q][p] = -sn * conj(ph);
+                J.m[q][q] = c * conj(ph);
+                mat3 Jd = m_dag(&J);
+                mat3 T = m_mul(&A, &J);
+                A = m_mul(&Jd, &T);
+                *E = m_mul(E, &J);
+            }
+    }
+    for (int i = 0; i < 3; ++i) lam[i] = creal(A.m[i][i]);
+}
+
+static cplx m_det(const mat3 *a) {
+    const cplx(*m)[3] = a->m;
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+           m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+/* P_ucp{V} = W / cbrt(det W), W = V (V^dag V)^{-1/2} (Eq. W), with the
+ * principal cube root: arg det W taken in (-pi, pi], so the phase divided
+ * out lies in (-pi/3, pi/3] (the paper's open interval, closed at +pi/3 to
+ * match the label convention at arg = pi).  Reading for a singular V (the
+ * projection is undefined): det(V^dag V) <= 1e-24 (Tr(V^dag V)/3)^3 returns
+ * 1 and leaves *out untouched. */
+static int ucp_project(const mat3 *V, mat3 *out) {
+    mat3 Vd = m_dag(V);
+    mat3 A = m_mul(&Vd, V);
+    double lam[3];
+    mat3 E;
+    herm_eig(&A, lam, &E);
+    double tr = lam[0] + lam[1] + lam[2];
+    if (!(lam[0] > 0.0 && lam[1] > 0.0 && lam[2] > 0.0) ||
+        !(lam[0] * lam[1] * lam[2] > 1e-24 * (tr / 3.0) * (tr / 3.0) * (tr / 3.0)))
+        return 1;
+    mat3 R = m_zero();     /* (V^dag V)^{-1/2} = E diag(lam^{-1/2}) E^dag */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) R.m[i][j] += E.m[i][k] * (1.0 / sqrt(lam[k])) * conj(E.m[j][k]);
+    mat3 W = m_mul(V, &R);
+    cplx d = m_det(&W);
+    double phi = atan2(cimag(d), creal(d));
+    if (phi <= -OR_PI) phi = OR_PI;
+    cplx f = cexp(-I * phi / 3.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) W.m[i][j] *= f;
+    *out = W;
+    return 0;
+}
+
+/* One projection of a single matrix (for the pins): 0, or 1 if singular. */
+int or_ucp(const double *V18, double *out18) {
+    mat3 V, P;
+    memcpy(&V, V18, sizeof V);
+    int r = ucp_project(&V, &P);
+    if (r == 0) memcpy(out18, &P, sizeof P);
+    return r;
+}
+
+/* n_sweeps of APE smearing with unit circle projection (Sec. II.C):
+ * V = (1 - alpha) U + (alpha / 6) Sigma(eps, u0) (Eq. V, staples of Eq.
+ * over-improvement), U <- P_ucp{V}.  schedule OR_SIMULTANEOUS is APE
+ * smearing (every link from the previous field); OR_ANNEALED is annealed
+ * U-link smearing with UCP (AUS+UCP, Sec. VII.A), in the colour order of
+ * or_smooth.  A singular V leaves the link.  vp / ref_labels / n_reject /
+ * gauge as in or_smooth (Sec. VI). */
+int or_ape_ucp(const int32_t dims[4], double *links, const int8_t *ref_labels, int n_sweeps, double alpha,
+               double eps, double u0, int schedule, int vp, int64_t *n_reject, int nthreads,
+               const double *gauge) {
+    lattice g;
+    if (lat_init(&g, dims)) return -1;
+    if (n_sweeps < 0) return -2;
+    for (int d = 0; d < 4; ++d)
+        if (schedule == OR_ANNEALED && g.L[d] % 4) return -3;
+    if (vp && !ref_labels) return -4;
+    double c0, c1;
+    or_overimproved_coeffs(eps, u0, &c0, &c1);
+    cplx *U = (cplx *)links;
+    const cplx *G = (const cplx *)gauge;
+    long *sites = (long *)malloc(sizeof(long) * g.V);
+    cplx *old = NULL;
+    if (schedule == OR_SIMULTANEOUS) old = (cplx *)malloc(sizeof(cplx) * 9 * 4 * g.V);
+    if (!sites || (schedule == OR_SIMULTANEOUS && !old)) { free(sites); free(old); return -5; }
+    if (nthreads < 1) nthreads = 1;
+    int err = 0;
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        int64_t rej = 0;
+        if (schedule == OR_SIMULTANEOUS) memcpy(old, U, sizeof(cplx) * 9 * 4 * g.V);
+        const cplx *src = schedule == OR_SIMULTANEOUS ? old : U;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int c = 0; c < (schedule == OR_ANNEALED ? 4 : 1); ++c) {
+                long n;
+                if (schedule == OR_ANNEALED) n = class_sites(&g, mu, c, sites);
+                else { n = g.V; for (long s = 0; s < n; ++s) sites[s] = s; }
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static) reduction(+ : rej) reduction(| : err)
+#endif
+                for (long i = 0; i < n; ++i) {
+                    int x[4];
+                    lat_coords(&g, sites[i], x);
+                    mat3 S;
+                    if (staple_sum(&g, src, mu, x, c0, c1, &S)) { err |= 1; continue; }
+                    mat3 Ux = link_get(&g, src, mu, sites[i]);
+                    mat3 Vb = m_zero();
+                    m_axpy(&Vb, 1.0 - alpha, &Ux);
+                    m_axpy(&Vb, alpha / 6.0, &S);
+                    mat3 Un;
+                    if (ucp_project(&Vb, &Un)) Un = Ux;
+                    if (vp && label_of_trace(vp_trace(g.L, g.V, G, mu, x, &Un)) !=
+                                  ref_labels[(long)mu * g.V + sites[i]]) {
+                        rej += 1;
+                        if (schedule == OR_SIMULTANEOUS) link_put(&g, U, mu, sites[i], &Ux);
+                        continue;
+                    }
+                    link_put(&g, U, mu, sites[i], &Un);
+                }
+            }
+        if (n_reject) n_reject[sw] = rej;
+    }
+    free(sites);
+    free(old);
+    return err ? -6 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wilson flow by a third-order Runge-Kutta scheme (Sec. V.B, Sec. VII.A)     */
+/* ------------------------------------------------------------------------ */
+
+/* The flow dU/dtau = Q[U] U of Sec. V.B, Q the generator of Eq. (generator)
+ * built from the staples Sigma(eps, u0) (eps = 1: the Wilson flow), over
+ * n_steps steps of size h with the third-order Runge-Kutta scheme of
+ * Luscher (JHEP 08 (2010) 071, Appendix C), which the paper names as the
+ * alternative to its Euler steps.  With Z_i = h Q[W_i] on every link:
+ *   W_0 = U(tau),
+ *   W_1 = exp(Z_0 / 4) W_0,
+ *   W_2 = exp(8 Z_1 / 9 - 17 Z_0 / 36) W_1,
+ *   U(tau + h) = W_3 = exp(3 Z_2 / 4 - 8 Z_1 / 9 + 17 Z_0 / 36) W_2.
+ * Every Z_i is taken from the whole field W_i before any link moves. */
+static int flow_generators(const lattice *g, const cplx *W, double c0, double c1, double h, mat3 *Z,
+                           int nthreads) {
+    int err = 0;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static) reduction(| : err)
+#endif
+    for (long i = 0; i < 4 * g->V; ++i) {
+        int mu = (int)(i / g->V);
+        long s = i % g->V;
+        int x[4];
+        lat_coords(g, s, x);
+        mat3 S;
+        if (staple_sum(g, W, mu, x, c0, c1, &S)) { err |= 1; continue; }
+        mat3 Ux = link_get(g, W, mu, s);
+        mat3 Ud = m_dag(&Ux);
+        mat3 Om = m_mul(&S, &Ud);
+        mat3 Omd = m_dag(&Om);
+        mat3 A = Om;
+        m_axpy(&A, -1.0, &Omd);
+        cplx trA = m_trace(&A);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Z[i].m[a][b] = h * (0.5 * A.m[a][b] - (a == b ? trA / 6.0 : 0.0));
+    }
+    return err;
+}
+
+static void flow_apply(const lattice *g, cplx *W, const mat3 *X, int nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+#endif
+    for (long i = 0; i < 4 * g->V; ++i) {
+        int mu = (int)(i / g->V);
+        long s = i % g->V;
+        mat3 E = expm_series(&X[i]);
+        mat3 Ux = link_get(g, W, mu, s);
+        mat3 Un = m_mul(&E, &Ux);
+        link_put(g, W, mu, s, &Un);
+    }
+}
+
+int or_flow_rk3(const int32_t dims[4], double *links, int n_steps, double h, double eps, double u0,
+                int nthreads) {
+    lattice g;
+    if (lat_init(&g, dims)) return -1;
+    if (n_steps < 0) return -2;
+    double c0, c1;
+    or_overimproved_coeffs(eps, u0, &c0, &c1);
+    if (nthreads < 1) nthreads = 1;
+    cplx *W = (cplx *)links;
+    const long n = 4 * g.V;
+    mat3 *Z0 = (mat3 *)malloc(sizeof(mat3) * n), *Z1 = (mat3 *)malloc(sizeof(mat3) * n);
+    mat3 *Z2 = (mat3 *)malloc(sizeof(mat3) * n), *X = (mat3 *)malloc(sizeof(mat3) * n);
+    if (!Z0 || !Z1 || !Z2 || !X) { free(Z0); free(Z1); free(Z2); free(X); return -5; }
+    int err = 0;
+    for (int st = 0; st < n_steps && !err; ++st) {
+        err |= flow_generators(&g, W, c0, c1, h, Z0, nthreads);
+        for (long i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) X[i].m[a][b] = 0.25 * Z0[i].m[a][b];
+        flow_apply(&g, W, X, nthreads);                                 /* W_1 */
+        err |= flow_generators(&g, W, c0, c1, h, Z1, nthreads);
+        for (long i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    X[i].m[a][b] = (8.0 / 9.0) * Z1[i].m[a][b] - (17.0 / 36.0) * Z0[i].m[a][b];
+        flow_apply(&g, W, X, nthreads);                                 /* W_2 */
+        err |= flow_generators(&g, W, c0, c1, h, Z2, nthreads);
+        for (long i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    X[i].m[a][b] = 0.75 * Z2[i].m[a][b] - (8.0 / 9.0) * Z1[i].m[a][b] +
+                                   (17.0 / 36.0) * Z0[i].m[a][b];
+        flow_apply(&g, W, X, nthreads);                                 /* W_3 */
+    }
+    free(Z0); free(Z1); free(Z2); free(X);
+    return err ? -6 : 0;
+}
+
 int or_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

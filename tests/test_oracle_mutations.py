@@ -64,9 +64,29 @@ MUTATIONS = [
      "if (vp && label_of_trace(tr) != label_of_trace(m_trace(&Ux))) {",
      pins.test_vortex_preservation_keeps_original_labels, ()),
     ("blocking weight of the staples",
-     "m_axpy(&Vb, alpha / 6.0, &S);",
-     "m_axpy(&Vb, alpha / 3.0, &S);",
+     "m_axpy(&Vb, alpha / 6.0, &S);\n                    mat3 Un = maxretr",
+     "m_axpy(&Vb, alpha / 3.0, &S);\n                    mat3 Un = maxretr",
      pins.test_aus_below_alpha_min_leaves_vortex_fields_unchanged, ()),
+    ("APE blocking weight before the unit circle projection",
+     "m_axpy(&Vb, alpha / 6.0, &S);\n                    mat3 Un;\n",
+     "m_axpy(&Vb, alpha / 4.0, &S);\n                    mat3 Un;\n",
+     pins.test_ape_ucp_blocking_weights_on_a_constant_field, ("simultaneous",)),
+    ("unit circle projection without the determinant phase",
+     "cplx f = cexp(-I * phi / 3.0);",
+     "cplx f = 1.0;",
+     pins.test_ucp_is_the_special_unitary_polar_factor, ()),
+    ("unit circle projection with (V^dag V)^-1",
+     "E.m[i][k] * (1.0 / sqrt(lam[k])) * conj(E.m[j][k])",
+     "E.m[i][k] * (1.0 / lam[k]) * conj(E.m[j][k])",
+     pins.test_ucp_is_the_special_unitary_polar_factor, ()),
+    ("Runge-Kutta stage coefficient",
+     "(8.0 / 9.0) * Z1[i].m[a][b] - (17.0 / 36.0)",
+     "(8.0 / 9.0) * Z1[i].m[a][b] - (17.0 / 35.0)",
+     pins.test_flow_rk3_is_third_order_and_euler_first_order, ()),
+    ("Runge-Kutta first stage weight",
+     "X[i].m[a][b] = 0.25 * Z0[i].m[a][b];",
+     "X[i].m[a][b] = 0.3 * Z0[i].m[a][b];",
+     pins.test_flow_rk3_is_third_order_and_euler_first_order, ()),
     ("vortex preservation ignores the random gauge",
      "    if (!G) return m_trace(Un);",
      "    return m_trace(Un);",

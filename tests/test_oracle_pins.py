@@ -807,3 +807,173 @@ def test_observables_are_gauge_invariant_and_vanish_on_pure_gauge():
     pg = O.gauge_transform(dims, I, G)
     SR, Q = O.observables(dims, pg)
     assert abs(SR) < 1e-13 and abs(Q) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Unit circle projection and APE / AUS with it (Sec. II.C)
+# --------------------------------------------------------------------------
+
+def _polar_su3(V):
+    """Independent route to P_ucp: the unitary polar factor from numpy's SVD
+    (V = u s vh -> W = u vh), divided by the principal cube root of det W."""
+    u, s, vh = np.linalg.svd(V)
+    W = u @ vh
+    phi = np.angle(np.linalg.det(W))
+    if phi <= -np.pi:
+        phi = np.pi
+    return W * np.exp(-1j * phi / 3)
+
+
+def test_ucp_is_the_special_unitary_polar_factor():
+    rng = np.random.default_rng(71)
+    worst = 0.0
+    for _ in range(300):
+        V = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        P = O.ucp(V)
+        worst = max(worst, np.abs(P - _polar_su3(V)).max())
+        assert np.abs(P.conj().T @ P - np.eye(3)).max() < 1e-12
+        assert abs(np.linalg.det(P) - 1) < 1e-12
+    assert worst < 1e-11
+
+
+def test_ucp_closed_forms():
+    """SU(3) matrices are fixed points; positive scale factors drop out; the
+    projection is gauge equivariant; and r e^{i theta} I projects onto the
+    centre element e^{-2 pi i k / 3} with theta + 2 pi k / 3 in (-pi/3, pi/3]
+    (the paper's vortex-link result)."""
+    Us = _rand_su3(20, 72)
+    Gs = _rand_su3(40, 73)
+    rng = np.random.default_rng(74)
+    for n in range(20):
+        assert np.abs(O.ucp(Us[n]) - Us[n]).max() < 1e-13
+        V = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        assert np.abs(O.ucp(3.7 * V) - O.ucp(V)).max() < 1e-12
+        G, H = Gs[2 * n], Gs[2 * n + 1]
+        assert np.abs(O.ucp(G @ V @ H.conj().T) - G @ O.ucp(V) @ H.conj().T).max() < 1e-12
+    for theta in np.linspace(-np.pi + 1e-3, np.pi, 41):
+        k = [kk for kk in (0, 1, 2, -1, -2) if -np.pi / 3 < theta + 2 * np.pi * kk / 3 <= np.pi / 3 + 1e-15][0]
+        P = O.ucp(2.5 * np.exp(1j * theta) * np.eye(3))
+        assert np.abs(P - np.exp(-2j * np.pi * k / 3) * np.eye(3)).max() < 1e-13
+
+
+def test_ucp_of_a_singular_matrix_is_undefined():
+    assert O.ucp(np.zeros((3, 3))) is None
+    V = np.diag([1.0, 2.0, 0.0]).astype(np.complex128)
+    assert O.ucp(V) is None
+
+
+def _constant_diagonal_field(dims, a, b):
+    V = int(np.prod(dims))
+    D = np.diag(np.exp(1j * np.array([a, b, -a - b])))
+    return np.broadcast_to(D, (4, V, 3, 3)).astype(np.complex128), D
+
+
+@pytest.mark.parametrize("schedule", ["annealed", "simultaneous"])
+def test_ape_ucp_blocking_weights_on_a_constant_field(schedule):
+    """All links equal to one diagonal D: every plaquette and rectangle path
+    equals D, so Sigma = (6 c0 + 18 c1) D and V = [(1 - alpha) + alpha (c0 +
+    3 c1)] D.  At eps = 5 (c0 = -5/3, c1 = 1/3) the factor changes sign at
+    alpha = 0.6: below, the projection returns D; above, a multiple of -D,
+    whose projection is D rotated by a non-trivial centre element.  A wrong
+    blocking weight moves the threshold across alpha = 0.55 or 0.65."""
+    dims = (4, 4, 4, 4)
+    U, D = _constant_diagonal_field(dims, 0.3, -0.7)
+    c0, c1 = O.overimproved_coeffs(5.0)
+    assert abs(c0 + 3 * c1 + 2 / 3) < 1e-15
+    # annealed: the first colour class of mu = 0 sees the constant field; later
+    # classes see moved links (and near the threshold, where V = 0.083 D, each
+    # projection amplifies rounding by ~17), so only that class is checked
+    if schedule == "annealed":
+        sel = np.zeros((4, int(np.prod(dims))), dtype=bool)
+        for s_ in range(sel.shape[1]):
+            x = np.unravel_index(s_, dims[::-1])[::-1]
+            sel[0, s_] = O.colour(dims, 0, x) == 0
+    else:
+        sel = np.ones((4, int(np.prod(dims))), dtype=bool)
+    lo, _ = O.ape_ucp(dims, U, None, 1, 0.55, eps=5.0, schedule=schedule, vp=False)
+    assert np.abs(lo[sel] - D).max() < 1e-13
+    hi, _ = O.ape_ucp(dims, U, None, 1, 0.65, eps=5.0, schedule=schedule, vp=False)
+    # det W = det(-D) = -1 sits on the branch cut of the principal cube root,
+    # so rounding picks e^{+2 pi i/3} or e^{-2 pi i/3}: either centre rotation
+    d_plus = np.abs(hi[sel] - D * np.exp(2j * np.pi / 3)).max(axis=(1, 2))
+    d_minus = np.abs(hi[sel] - D * np.exp(-2j * np.pi / 3)).max(axis=(1, 2))
+    assert (np.minimum(d_plus, d_minus) < 1e-13).all()
+
+
+def test_ape_ucp_on_vortex_fields_moves_only_between_centre_elements():
+    """A Z(3) field in a random gauge: the blocked matrix of every link is
+    r e^{i theta} G(x) G^dag(x+mu), so a projected link is again G(x) z G^dag(x+mu)
+    with z in Z(3) (Sec. II.C); at small alpha z is the original element."""
+    dims = (4, 4, 4, 8)
+    lab = synth.iid_labels(dims, 75)
+    Z = O.links_from_labels(dims, lab)
+    G = synth.random_gauge(dims, 76)
+    ZG = O.gauge_transform(dims, Z, G)
+    for alpha, sched in [(0.02, "annealed"), (0.7, "annealed"), (0.7, "simultaneous")]:
+        out, _ = O.ape_ucp(dims, ZG, None, 1, alpha, eps=-0.25, schedule=sched, vp=False)
+        back = O.gauge_transform(dims, out, G.conj().transpose(0, 2, 1))
+        diag = back[..., [0, 1, 2], [0, 1, 2]]
+        assert np.abs(back - diag[..., :, None] * np.eye(3)).max() < 1e-12
+        assert np.abs(diag - diag[..., :1]).max() < 1e-12
+        n = np.rint(np.angle(diag[..., 0]) / (2 * np.pi / 3)).astype(int)
+        assert np.abs(diag[..., 0] - np.exp(2j * np.pi * n / 3)).max() < 1e-12
+        if alpha < 0.1:
+            assert np.array_equal(((n + 1) % 3) - 1, lab)
+
+
+def test_ape_ucp_gauge_equivariance_and_alpha_zero():
+    dims = (4, 4, 4, 4)
+    U = O.cool(dims, synth.haar_field(dims, 77), 2)
+    G = synth.random_gauge(dims, 78)
+    for sched in ("annealed", "simultaneous"):
+        a, _ = O.ape_ucp(dims, U, None, 2, 0.4, eps=-0.25, schedule=sched, vp=False)
+        b, _ = O.ape_ucp(dims, O.gauge_transform(dims, U, G), None, 2, 0.4, eps=-0.25, schedule=sched,
+                         vp=False)
+        assert np.abs(O.gauge_transform(dims, a, G) - b).max() < 1e-12
+        z, _ = O.ape_ucp(dims, U, None, 1, 0.0, schedule=sched, vp=False)
+        assert np.abs(z - U).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Runge-Kutta Wilson flow (Sec. V.B)
+# --------------------------------------------------------------------------
+
+def test_flow_rk3_is_third_order_and_euler_first_order():
+    """Flow to tau = 0.2 from a rough field: halving the step divides the
+    third-order scheme's error by ~8 and the Euler (simultaneous stout) error
+    by ~2, measured against a 512-step RK3 reference (ratios 8.8, 8.4 for 8 ->
+    16 -> 32 steps, approaching 8 from above).  A wrong stage coefficient
+    drops the order to 2 or 1."""
+    dims = (4, 4, 4, 4)
+    U = O.cool(dims, synth.haar_field(dims, 79), 3)
+    T = 0.2
+    ref = O.flow_rk3(dims, U, 512, T / 512)
+    e_rk = [np.abs(O.flow_rk3(dims, U, n, T / n) - ref).max() for n in (8, 16, 32)]
+    e_eu = [np.abs(O.smooth(dims, U, None, n, T / n, schedule=O.SIMULTANEOUS, vp=False)[0] - ref).max()
+            for n in (8, 16, 32)]
+    for a, b in zip(e_rk, e_rk[1:]):
+        assert 7.5 < a / b < 9.5
+    for a, b in zip(e_eu, e_eu[1:]):
+        assert 1.8 < a / b < 2.2
+
+
+def test_flow_rk3_invariants():
+    """A centre-vortex field in any gauge does not flow (Sec. V.B); the flow
+    is gauge equivariant, stays in SU(3) and lowers the Wilson action."""
+    dims = (4, 4, 4, 4)
+    lab = synth.iid_labels(dims, 80)
+    G = synth.random_gauge(dims, 81)
+    ZG = O.gauge_transform(dims, O.links_from_labels(dims, lab), G)
+    assert np.abs(O.flow_rk3(dims, ZG, 3, 0.05) - ZG).max() < 1e-14
+    U = O.cool(dims, synth.haar_field(dims, 82), 1)
+    a = O.flow_rk3(dims, U, 3, 0.03)
+    b = O.flow_rk3(dims, O.gauge_transform(dims, U, G), 3, 0.03)
+    assert np.abs(O.gauge_transform(dims, a, G) - b).max() < 1e-12
+    assert np.abs(np.einsum("...ji,...jk->...ik", a.conj(), a) - np.eye(3)).max() < 1e-12
+    assert np.abs(np.linalg.det(a) - 1).max() < 1e-12
+    S = [O.action(dims, U)]
+    W = U
+    for _ in range(5):
+        W = O.flow_rk3(dims, W, 1, 0.02)
+        S.append(O.action(dims, W))
+    assert all(s1 < s0 for s0, s1 in zip(S, S[1:]))
