@@ -128,7 +128,7 @@ typedef struct {
     int64_t n_fp64_exp;           /* FP32 mode: exponentials redone in FP64 (|rho Q| large) */
     double action;                /* <S>/beta after the sweep, when recorded */
     int32_t has_action;
-    int32_t pad;
+    int32_t n_singular;           /* vs_smooth_ape: blocked matrices with no projection (link kept) */
 } vs_sweep_stats;
 
 /* n_sweeps of stout smoothing, Eqs. (stout)/(generator), with
@@ -159,6 +159,37 @@ vs_status vs_smooth(vs_field *f, int32_t n_sweeps, double rho, double epsilon, d
 vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, double epsilon, double u0,
                         int32_t n_hits, int32_t reunit_every, int32_t vortex_preserve,
                         vs_sweep_stats *stats);
+
+/* n_sweeps of APE blocking with unit circle projection (Sec. II.C, Eqs. V, W
+ * and P_ucp): V = (1 - alpha) U + (alpha / 6) Sigma(eps, u0) with the staples
+ * of Eq. over-improvement, U <- W / cbrt(det W), W = V (V^dag V)^{-1/2}, the
+ * principal cube root (arg det W in (-pi, pi]).  schedule VS_SIMULTANEOUS
+ * is APE smearing (every link from the previous sweep's field);
+ * VS_ANNEALED is annealed U-link smearing with UCP (AUS+UCP, Sec. VII.A), in
+ * the colour order of vs_smooth.  A blocked matrix with
+ * det(V^dag V) <= 1e-24 (Tr(V^dag V)/3)^3 has no projection: the link is kept
+ * and counted in stats[].n_singular.  vortex_preserve: Sec. VI test against
+ * the original labels.  FP32: re-unitarise every reunit_every sweeps (0 =
+ * never).  stats as for vs_smooth (no action).  EINVAL: alpha outside
+ * [0, 1], bad schedule, non-finite eps, u0 <= 0. */
+vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, double epsilon, double u0,
+                        int32_t schedule, int32_t reunit_every, int32_t vortex_preserve,
+                        vs_sweep_stats *stats);
+
+/* n_steps of the Wilson flow dU/dtau = Q[U] U (Sec. V.B; Q of Eq. generator
+ * with the staples Sigma(eps, u0), eps = 1: the Wilson flow) by the
+ * third-order Runge-Kutta scheme of Luscher (JHEP 08 (2010) 071), step size
+ * `step`: with Z_i = step Q[W_i] on every link,
+ *   W_1 = exp(Z_0/4) W_0, W_2 = exp(8 Z_1/9 - 17 Z_0/36) W_1,
+ *   U(tau + step) = exp(3 Z_2/4 - 8 Z_1/9 + 17 Z_0/36) W_2,
+ * each stage from the whole field of the previous one.  Allocates a
+ * 4 x 9 x V exponent buffer (field precision) on first use, kept with the
+ * field.  No vortex preservation (the flow of a centre-vortex field is
+ * trivial, Sec. V.B).  FP32: re-unitarise every reunit_every steps.  stats:
+ * NULL or [n_steps] (n_fp64_exp per step).  EINVAL: step < 0 or non-finite,
+ * non-finite eps, u0 <= 0. */
+vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, double epsilon, double u0,
+                      int32_t reunit_every, vs_sweep_stats *stats);
 
 /* One colour class (mu, colour) of the annealed schedule, as vs_smooth runs it. */
 vs_status vs_subsweep(vs_field *f, int32_t mu, int32_t colour, double rho, double epsilon,

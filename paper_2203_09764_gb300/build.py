@@ -22,7 +22,8 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
 # class-update kernel, which sets its register budget)
 FLAGS += os.environ.get("VS_NVCC_EXTRA", "").split()
 
-SOURCES = ["vs_sweep_f18.cu", "vs_sweep_f12.cu", "vs_sweep_d18.cu", "vs_kernels.cu",
+SOURCES = ["vs_sweep_f18.cu", "vs_sweep_f12.cu", "vs_sweep_d18.cu", "vs_ape_f18.cu", "vs_ape_f12.cu",
+           "vs_ape_d18.cu", "vs_kernels.cu",
            "vs_api.cu", "vs_serve.cu", "vs_noalloc.cu"]
 
 

@@ -173,6 +173,7 @@ extern "C" void vs_field_destroy(vs_field *f) {
     dev_free(f->ctx, f->G);
     dev_free(f->ctx, f->partials);
     dev_free(f->ctx, f->scratch);
+    dev_free(f->ctx, f->flowS);
     dev_free(f->ctx, f->sweep_counts);
     dev_free(f->ctx, f->sweep_actions);
     for (auto &e : f->events) cudaEventDestroy(e);
@@ -630,6 +631,177 @@ extern "C" vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, 
         memset(&stats[s], 0, sizeof stats[s]);
         stats[s].n_reject = (int64_t)cnt[2 * s];
         stats[s].n_accept = 4ll * f->g.V - stats[s].n_reject;
+    }
+    return check_device_error(f);
+}
+
+// ---------------------------------------------------------------------------
+// APE / AUS with unit circle projection, Runge-Kutta Wilson flow
+// ---------------------------------------------------------------------------
+
+static cudaError_t ape_launch(vs_field *f, bool rect, int mu, const ApeParams &p) {
+    if (f->prec == VS_FP64) return launch_ape_d18(rect, mu, p, f->stream);
+    if (f->nc == 12) return launch_ape_f12(rect, mu, p, f->stream);
+    return launch_ape_f18(rect, mu, p, f->stream);
+}
+
+static cudaError_t flow_launch(vs_field *f, bool rect, int mu, const FlowParams &p) {
+    if (f->prec == VS_FP64) return launch_flow_d18(rect, mu, p, f->stream);
+    if (f->nc == 12) return launch_flow_f12(rect, mu, p, f->stream);
+    return launch_flow_f18(rect, mu, p, f->stream);
+}
+
+// per-sweep counter pairs in the field's stats buffer
+static vs_status ensure_sweep_counts(vs_field *f, int32_t n, const char *who) {
+    if (f->sweep_cap >= n) return VS_OK;
+    CK(cudaStreamSynchronize(f->stream));
+    dev_free(f->ctx, f->sweep_counts);
+    dev_free(f->ctx, f->sweep_actions);
+    f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, 2 * sizeof(unsigned long long) * n);
+    f->sweep_actions = (double *)dev_alloc(f->ctx, sizeof(double) * n);
+    if (!f->sweep_counts || !f->sweep_actions) {
+        f->sweep_cap = 0;
+        return fail(VS_ENOMEM, "%s: stats allocation failed", who);
+    }
+    f->sweep_cap = n;
+    return VS_OK;
+}
+
+extern "C" vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, double epsilon, double u0,
+                                   int32_t schedule, int32_t reunit_every, int32_t vortex_preserve,
+                                   vs_sweep_stats *stats) {
+    if (!f) return fail(VS_EINVAL, "vs_smooth_ape: NULL field");
+    if (n_sweeps < 0 || reunit_every < 0) return fail(VS_EINVAL, "vs_smooth_ape: bad count");
+    if (schedule != VS_ANNEALED && schedule != VS_SIMULTANEOUS) return fail(VS_EINVAL, "vs_smooth_ape: bad schedule");
+    if (!std::isfinite(alpha) || !(alpha >= 0.0 && alpha <= 1.0) || !std::isfinite(epsilon) || !(u0 > 0))
+        return fail(VS_EINVAL, "vs_smooth_ape: need 0 <= alpha <= 1, finite eps, u0 > 0");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_smooth_ape: field not loaded");
+    CK(cudaSetDevice(f->ctx->opt.device));
+    const bool rect = epsilon != 1.0;
+    vs_status st;
+    if (stats) {
+        if ((st = ensure_sweep_counts(f, n_sweeps, "vs_smooth_ape"))) return st;
+        if (n_sweeps > 0)
+            CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_sweeps, f->stream));
+    }
+    if (schedule == VS_SIMULTANEOUS && (st = ensure_scratch(f, field_bytes(f)))) return st;
+    ApeParams a;
+    memset(&a, 0, sizeof a);
+    a.g = f->g;
+    a.U = f->U;
+    a.ref = f->ref;
+    a.G = f->gauge_on ? f->G : nullptr;
+    a.alpha = alpha;
+    a.c0 = (5.0 - 2.0 * epsilon) / 3.0;
+    a.c1 = (epsilon - 1.0) / (12.0 * u0 * u0);
+    a.alpha_f = (float)a.alpha;
+    a.c0_f = (float)a.c0;
+    a.c1_f = (float)a.c1;
+    a.vp = vortex_preserve ? 1 : 0;
+    for (int s = 0; s < n_sweeps; ++s) {
+        a.counters = stats ? f->sweep_counts + 2 * s : nullptr;
+        if (schedule == VS_ANNEALED) {
+            a.Usrc = f->U;
+            a.n_threads = f->g.V / 4;
+            for (int mu = 0; mu < 4; ++mu)
+                for (int c = 0; c < 4; ++c) {
+                    a.colour = c;
+                    CK(ape_launch(f, rect, mu, a));
+                }
+        } else {
+            CK(cudaMemcpyAsync(f->scratch, f->U, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
+            a.Usrc = f->scratch;
+            a.colour = -1;
+            a.n_threads = f->g.V;
+            for (int mu = 0; mu < 4; ++mu) CK(ape_launch(f, rect, mu, a));
+        }
+        if (f->prec == VS_FP32 && reunit_every > 0 && (f->sweeps_done + s + 1) % reunit_every == 0)
+            CK(launch_reunit(1, f->nc, f->g, f->U, vortex_preserve ? f->ref : nullptr, f->stream,
+                             f->gauge_on ? f->G : nullptr));
+    }
+    f->sweeps_done += n_sweeps;
+    if (!stats) return VS_OK;
+    std::vector<unsigned long long> cnt(2 * (size_t)n_sweeps);
+    if (n_sweeps > 0)
+        CK(cudaMemcpyAsync(cnt.data(), f->sweep_counts, cnt.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    for (int s = 0; s < n_sweeps; ++s) {
+        memset(&stats[s], 0, sizeof stats[s]);
+        stats[s].n_reject = (int64_t)cnt[2 * s];
+        stats[s].n_accept = 4ll * f->g.V - stats[s].n_reject;
+        stats[s].n_singular = (int32_t)cnt[2 * s + 1];
+    }
+    return check_device_error(f);
+}
+
+extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, double epsilon, double u0,
+                                 int32_t reunit_every, vs_sweep_stats *stats) {
+    if (!f) return fail(VS_EINVAL, "vs_flow_rk3: NULL field");
+    if (n_steps < 0 || reunit_every < 0) return fail(VS_EINVAL, "vs_flow_rk3: bad count");
+    vs_status st = check_smooth_params(step, epsilon, u0);
+    if (st) return st;
+    if (!(step >= 0.0)) return fail(VS_EINVAL, "vs_flow_rk3: step must be >= 0");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_flow_rk3: field not loaded");
+    CK(cudaSetDevice(f->ctx->opt.device));
+    const bool rect = epsilon != 1.0;
+    if ((st = ensure_scratch(f, field_bytes(f)))) return st;
+    const size_t sbytes = 4ull * 9 * f->g.P * (f->prec == VS_FP32 ? sizeof(float) : sizeof(double));
+    if (f->flowS_bytes < sbytes) {
+        CK(cudaStreamSynchronize(f->stream));
+        dev_free(f->ctx, f->flowS);
+        f->flowS = dev_alloc(f->ctx, sbytes);
+        f->flowS_bytes = f->flowS ? sbytes : 0;
+        if (!f->flowS) return fail(VS_ENOMEM, "vs_flow_rk3: exponent buffer of %zu bytes failed", sbytes);
+    }
+    if (stats) {
+        if ((st = ensure_sweep_counts(f, n_steps, "vs_flow_rk3"))) return st;
+        if (n_steps > 0)
+            CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_steps, f->stream));
+    }
+    // Luscher's third-order scheme in the low-storage form: stage k uses
+    // H_S <- a_k H_Z + b_k H_S and W <- exp(i c_k H_S) W with
+    // (a, b, c) = (1, 0, 1/4), (8/9, -17/36, 1), (3/4, -1, 1).
+    static const double A[3] = {1.0, 8.0 / 9.0, 0.75}, B[3] = {0.0, -17.0 / 36.0, -1.0}, C[3] = {0.25, 1.0, 1.0};
+    FlowParams p;
+    memset(&p, 0, sizeof p);
+    p.g = f->g;
+    p.U = f->U;
+    p.Usrc = f->scratch;
+    p.S = f->flowS;
+    p.n_threads = f->g.V;
+    p.h = step;
+    p.c0 = (5.0 - 2.0 * epsilon) / 3.0;
+    p.c1 = (epsilon - 1.0) / (12.0 * u0 * u0);
+    p.h_f = (float)p.h;
+    p.c0_f = (float)p.c0;
+    p.c1_f = (float)p.c1;
+    for (int s = 0; s < n_steps; ++s) {
+        p.counters = stats ? f->sweep_counts + 2 * s : nullptr;
+        for (int k = 0; k < 3; ++k) {
+            p.a = A[k];
+            p.b = B[k];
+            p.c = C[k];
+            p.a_f = (float)p.a;
+            p.b_f = (float)p.b;
+            p.c_f = (float)p.c;
+            CK(cudaMemcpyAsync(f->scratch, f->U, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
+            for (int mu = 0; mu < 4; ++mu) CK(flow_launch(f, rect, mu, p));
+        }
+        if (f->prec == VS_FP32 && reunit_every > 0 && (f->sweeps_done + s + 1) % reunit_every == 0)
+            CK(launch_reunit(1, f->nc, f->g, f->U, nullptr, f->stream, nullptr));
+    }
+    f->sweeps_done += n_steps;
+    if (!stats) return VS_OK;
+    std::vector<unsigned long long> cnt(2 * (size_t)n_steps);
+    if (n_steps > 0)
+        CK(cudaMemcpyAsync(cnt.data(), f->sweep_counts, cnt.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    for (int s = 0; s < n_steps; ++s) {
+        memset(&stats[s], 0, sizeof stats[s]);
+        stats[s].n_accept = 4ll * f->g.V;
+        stats[s].n_fp64_exp = (int64_t)cnt[2 * s + 1];
     }
     return check_device_error(f);
 }

@@ -46,6 +46,8 @@ struct vs_field {
     unsigned long long *d_counts = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    void *flowS = nullptr;          // Runge-Kutta exponent H_S, 9 reals per link
+    size_t flowS_bytes = 0;
     unsigned long long *sweep_counts = nullptr;
     double *sweep_actions = nullptr;
     int sweep_cap = 0;

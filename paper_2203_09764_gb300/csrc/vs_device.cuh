@@ -199,23 +199,23 @@ __device__ __forceinline__ M3<T> m3_mul(const M3<T> &a, const M3<T> &b) {
     M3<T> r;
     if constexpr (sizeof(T) == 4 && VS_FFMA2) {
         m3_mul_f32<false>(r, a, b);
-        return r;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            T sr = T(0), si = T(0);
+            for (int j = 0; j < 3; ++j) {
+                T sr = T(0), si = T(0);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                sr = fma(a.re[i * 3 + k], b.re[k * 3 + j], sr);
-                sr = fma(-a.im[i * 3 + k], b.im[k * 3 + j], sr);
-                si = fma(a.re[i * 3 + k], b.im[k * 3 + j], si);
-                si = fma(a.im[i * 3 + k], b.re[k * 3 + j], si);
+                for (int k = 0; k < 3; ++k) {
+                    sr = fma(a.re[i * 3 + k], b.re[k * 3 + j], sr);
+                    sr = fma(-a.im[i * 3 + k], b.im[k * 3 + j], sr);
+                    si = fma(a.re[i * 3 + k], b.im[k * 3 + j], si);
+                    si = fma(a.im[i * 3 + k], b.re[k * 3 + j], si);
+                }
+                r.re[i * 3 + j] = sr;
+                r.im[i * 3 + j] = si;
             }
-            r.re[i * 3 + j] = sr;
-            r.im[i * 3 + j] = si;
-        }
+    }
     return r;
 }
 
@@ -224,23 +224,23 @@ template <class T>
 __device__ __forceinline__ void m3_madd(M3<T> &r, const M3<T> &a, const M3<T> &b) {
     if constexpr (sizeof(T) == 4 && VS_FFMA2) {
         m3_mul_f32<true>(r, a, b);
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            T sr = r.re[i * 3 + j], si = r.im[i * 3 + j];
+            for (int j = 0; j < 3; ++j) {
+                T sr = r.re[i * 3 + j], si = r.im[i * 3 + j];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                sr = fma(a.re[i * 3 + k], b.re[k * 3 + j], sr);
-                sr = fma(-a.im[i * 3 + k], b.im[k * 3 + j], sr);
-                si = fma(a.re[i * 3 + k], b.im[k * 3 + j], si);
-                si = fma(a.im[i * 3 + k], b.re[k * 3 + j], si);
+                for (int k = 0; k < 3; ++k) {
+                    sr = fma(a.re[i * 3 + k], b.re[k * 3 + j], sr);
+                    sr = fma(-a.im[i * 3 + k], b.im[k * 3 + j], sr);
+                    si = fma(a.re[i * 3 + k], b.im[k * 3 + j], si);
+                    si = fma(a.im[i * 3 + k], b.re[k * 3 + j], si);
+                }
+                r.re[i * 3 + j] = sr;
+                r.im[i * 3 + j] = si;
             }
-            r.re[i * 3 + j] = sr;
-            r.im[i * 3 + j] = si;
-        }
+    }
 }
 
 // r = a * b^dagger

@@ -43,6 +43,44 @@ struct AusParams {
     unsigned long long *counters;  // [0] rejects (may be null)
 };
 
+// One colour class (or, colour < 0, every link of direction mu) of APE
+// blocking with unit circle projection (Sec. II.C): V = (1 - alpha) U +
+// (alpha / 6) Sigma(eps), U <- P_ucp{V}; optional vortex preservation.
+struct ApeParams {
+    Geo g;
+    void *U;             // destination (in place for the annealed schedule)
+    const void *Usrc;    // blocking source: == U (annealed) or the previous field
+    const int8_t *ref;
+    const void *G;       // random gauge transformation or null
+    int colour;
+    int n_threads;
+    double alpha, c0, c1;
+    float alpha_f, c0_f, c1_f;
+    int vp;
+    unsigned long long *counters;  // [0] rejects, [1] singular blocked matrices (may be null)
+};
+
+// One stage of the third-order Runge-Kutta Wilson flow for every link of
+// direction mu: with H_Z the Hermitian form of h Q[W_i] (Eq. generator),
+// H_S <- a H_Z + b H_S (b = 0: H_S not read), W_{i+1} = exp(i c H_S) W_i.
+struct FlowParams {
+    Geo g;
+    void *U;             // W_{i+1}
+    const void *Usrc;    // W_i
+    void *S;             // H_S, 9 reals per link [mu][9][P] in the field precision
+    int n_threads;
+    double h, a, b, c, c0, c1;
+    float h_f, a_f, b_f, c_f, c0_f, c1_f;
+    unsigned long long *counters;  // [1] FP64 exponentials (may be null)
+};
+
+cudaError_t launch_ape_f18(bool rect, int mu, const ApeParams &p, cudaStream_t st);
+cudaError_t launch_ape_f12(bool rect, int mu, const ApeParams &p, cudaStream_t st);
+cudaError_t launch_ape_d18(bool rect, int mu, const ApeParams &p, cudaStream_t st);
+cudaError_t launch_flow_f18(bool rect, int mu, const FlowParams &p, cudaStream_t st);
+cudaError_t launch_flow_f12(bool rect, int mu, const FlowParams &p, cudaStream_t st);
+cudaError_t launch_flow_d18(bool rect, int mu, const FlowParams &p, cudaStream_t st);
+
 cudaError_t launch_aus_f18(bool rect, int mu, const AusParams &p, cudaStream_t st);
 cudaError_t launch_aus_f12(bool rect, int mu, const AusParams &p, cudaStream_t st);
 cudaError_t launch_aus_d18(bool rect, int mu, const AusParams &p, cudaStream_t st);

@@ -283,22 +283,31 @@ __device__ __forceinline__ M3<T> exp_iH(T h00, T h11, T h22, T h01r, T h01i, T h
     return Mx;
 }
 
+// H = -i rho Q for staple sum sig and link Ux (Eq. generator: Omega = sig
+// Ux^dag, Q its traceless anti-Hermitian part), as its diagonal and upper
+// entries h[0..8] = (h00, h11, h22, h01r, h01i, h02r, h02i, h12r, h12i).
+// Diagonal rho (Im Om_jj - (1/3) sum_l Im Om_ll), written so that equal
+// diagonal entries give exactly zero; off-diagonal
+// H_jk = (rho/2) [(Im Om_jk + Im Om_kj) - i (Re Om_jk - Re Om_kj)].
+template <class T>
+__device__ __forceinline__ void stout_H(const M3<T> &sig, const M3<T> &Ux, T rho, T h[9]) {
+    M3<T> Om = m3_mul_nd(sig, Ux);
+    const T third = T(1) / T(3);
+    h[0] = rho * ((T(2) * Om.im[0] - Om.im[4] - Om.im[8]) * third);
+    h[1] = rho * ((T(2) * Om.im[4] - Om.im[0] - Om.im[8]) * third);
+    h[2] = rho * ((T(2) * Om.im[8] - Om.im[0] - Om.im[4]) * third);
+    const T hr = T(0.5) * rho;
+    h[3] = hr * (Om.im[1] + Om.im[3]); h[4] = -hr * (Om.re[1] - Om.re[3]);
+    h[5] = hr * (Om.im[2] + Om.im[6]); h[6] = -hr * (Om.re[2] - Om.re[6]);
+    h[7] = hr * (Om.im[5] + Om.im[7]); h[8] = -hr * (Om.re[5] - Om.re[7]);
+}
+
 // Candidate U' = exp(rho Q) U for staple sum sig.
 template <class T>
 __device__ __forceinline__ M3<T> stout_candidate(const M3<T> &sig, const M3<T> &Ux, T rho, bool &fp64_used) {
-    M3<T> Om = m3_mul_nd(sig, Ux);
-    // H = -i rho Q: diagonal rho (Im Om_jj - (1/3) sum_l Im Om_ll), written so
-    // that equal diagonal entries give exactly zero; off-diagonal
-    // H_jk = (rho/2) [(Im Om_jk + Im Om_kj) - i (Re Om_jk - Re Om_kj)].
-    const T third = T(1) / T(3);
-    const T h00 = rho * ((T(2) * Om.im[0] - Om.im[4] - Om.im[8]) * third);
-    const T h11 = rho * ((T(2) * Om.im[4] - Om.im[0] - Om.im[8]) * third);
-    const T h22 = rho * ((T(2) * Om.im[8] - Om.im[0] - Om.im[4]) * third);
-    const T hr = T(0.5) * rho;
-    const T h01r = hr * (Om.im[1] + Om.im[3]), h01i = -hr * (Om.re[1] - Om.re[3]);
-    const T h02r = hr * (Om.im[2] + Om.im[6]), h02i = -hr * (Om.re[2] - Om.re[6]);
-    const T h12r = hr * (Om.im[5] + Om.im[7]), h12i = -hr * (Om.re[5] - Om.re[7]);
-    M3<T> Mx = exp_iH<T>(h00, h11, h22, h01r, h01i, h02r, h02i, h12r, h12i, fp64_used);
+    T h[9];
+    stout_H<T>(sig, Ux, rho, h);
+    M3<T> Mx = exp_iH<T>(h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8], fp64_used);
     return m3_mul(Mx, Ux);
 }
 

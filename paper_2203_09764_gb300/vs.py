@@ -50,7 +50,7 @@ class vs_anneal(ctypes.Structure):
 class vs_sweep_stats(ctypes.Structure):
     _fields_ = [("n_accept", ctypes.c_int64), ("n_reject", ctypes.c_int64),
                 ("n_fp64_exp", ctypes.c_int64), ("action", ctypes.c_double),
-                ("has_action", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("has_action", ctypes.c_int32), ("n_singular", ctypes.c_int32)]
 
 
 class vs_vortex_report(ctypes.Structure):
@@ -111,6 +111,10 @@ _SIGS = {
                                    ctypes.c_double, ctypes.POINTER(vs_anneal), ctypes.c_int32, P]),
     "vs_smooth_aus": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]),
+    "vs_smooth_ape": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]),
+    "vs_flow_rk3": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int32, P]),
     "vs_subsweep": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "vs_vortex_check": (ctypes.c_int32, [P, ctypes.POINTER(vs_vortex_report)]),
@@ -314,6 +318,31 @@ def vs_smooth_aus(f, n_sweeps, alpha, epsilon=-0.25, u0=1.0, n_hits=3, reunit_ev
     if not stats:
         return None
     return [dict(n_accept=s.n_accept, n_reject=s.n_reject) for s in st[:int(n_sweeps)]]
+
+
+def vs_smooth_ape(f, n_sweeps, alpha, epsilon=-0.25, u0=1.0, schedule=None, reunit_every=10,
+                  vortex_preserve=True, stats=False):
+    """APE blocking with unit circle projection: schedule VS_ANNEALED (AUS+UCP,
+    the default) or VS_SIMULTANEOUS (APE smearing)."""
+    sched = VS_ANNEALED if schedule is None else int(schedule)
+    st = (vs_sweep_stats * max(int(n_sweeps), 1))() if stats else None
+    _check(lib.vs_smooth_ape(f, int(n_sweeps), float(alpha), float(epsilon), float(u0), sched,
+                             int(reunit_every), 1 if vortex_preserve else 0,
+                             ctypes.cast(st, ctypes.c_void_p) if stats else None))
+    if not stats:
+        return None
+    return [dict(n_accept=s.n_accept, n_reject=s.n_reject, n_singular=s.n_singular)
+            for s in st[:int(n_sweeps)]]
+
+
+def vs_flow_rk3(f, n_steps, step, epsilon=1.0, u0=1.0, reunit_every=10, stats=False):
+    """Wilson flow (staples Sigma(eps, u0)) by third-order Runge-Kutta."""
+    st = (vs_sweep_stats * max(int(n_steps), 1))() if stats else None
+    _check(lib.vs_flow_rk3(f, int(n_steps), float(step), float(epsilon), float(u0), int(reunit_every),
+                           ctypes.cast(st, ctypes.c_void_p) if stats else None))
+    if not stats:
+        return None
+    return [dict(n_fp64_exp=s.n_fp64_exp) for s in st[:int(n_steps)]]
 
 
 def vs_subsweep(f, mu, colour, rho, epsilon=1.0, u0=1.0, vortex_preserve=True):
