@@ -275,6 +275,13 @@ def run_ours(args):
         except Exception as e:  # report it, keep the main line
             line["fp64_plain"] = {"error": repr(e)}
 
+    # ---- the paper's other smoothing paths on the same field ---------------
+    if not args.no_other:
+        try:
+            line["other_paths"] = other_paths(vs, ctx, stream, labels_dev, args, world, dev)
+        except Exception as e:
+            line["other_paths"] = {"error": repr(e)}
+
     # ---- serving: continuous batching of a Poisson job mix -----------------
     if not args.no_serve and rank == 0:
         try:
@@ -349,6 +356,47 @@ def fp64_plain(vs, ctx, stream, labels_dev, args, value, world, dev):
     v64 = world * n_links * n64 / (ms64 / 1e3)
     return {"value": v64, "unit": "link-updates/s", "sweeps": n64, "ms": ms64,
             "fp32_over_fp64": value / v64}
+
+
+def other_paths(vs, ctx, stream, labels_dev, args, world, dev):
+    """The paper's other smoothers on the benchmark field (FP32 18-real,
+    centrifuged): time per sweep (RK3: per step of three stages) with CUDA
+    events on the field's stream, after one untimed sweep."""
+    import torch
+    V = int(np.prod(DIMS))
+    n = args.other_sweeps
+    paths = {
+        "euler_wilson_flow": ("annealed stout, eps=1, rho=0.06 (Euler Wilson flow), VP",
+                              lambda f, k: vs.vs_smooth(f, k, RHO, 1.0, U0, reunit_every=REUNIT), 1),
+        "aus_maxretr": ("AUS, MaxReTr 3 hits, alpha=0.02, eps=-0.25, VP",
+                        lambda f, k: vs.vs_smooth_aus(f, k, 0.02, EPS, U0), 1),
+        "aus_ucp": ("AUS with unit circle projection, alpha=0.02, eps=-0.25, VP",
+                    lambda f, k: vs.vs_smooth_ape(f, k, 0.02, EPS, U0), 1),
+        "ape_ucp": ("APE smearing (simultaneous) with unit circle projection, alpha=0.5, eps=-0.25",
+                    lambda f, k: vs.vs_smooth_ape(f, k, 0.5, EPS, U0, schedule=vs.VS_SIMULTANEOUS,
+                                                  vortex_preserve=False), 1),
+        "rk3_wilson_flow": ("Wilson flow, third-order Runge-Kutta, eps=1, step 0.02 (3 stages per step)",
+                            lambda f, k: vs.vs_flow_rk3(f, k, 0.02, 1.0, U0), 3),
+    }
+    out = {}
+    for name, (what, run, passes) in paths.items():
+        f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK18, stream)
+        vs.vs_load_field(f, labels=labels_dev)
+        vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+        run(f, 1)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(f, n)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        vs.vs_field_destroy(f)
+        out[name] = {"what": what, "sweeps": n, "ms_per_sweep": ms / n,
+                     "link_updates_per_s": world * 4 * V * passes * n / (ms / 1e3),
+                     "sweeps_per_s": world * n / (ms / 1e3)}
+    return out
 
 
 def run_serving(vs, device, args):
@@ -500,6 +548,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip timing the other smoothing paths (AUS, UCP, Runge-Kutta flow)")
+    ap.add_argument("--other-sweeps", type=int, default=10)
     ap.add_argument("--scaling", action="store_true",
                     help="lattice-size sweep 16^3x32 .. 48^3x96 instead of the benchmark step")
     args = ap.parse_args()
