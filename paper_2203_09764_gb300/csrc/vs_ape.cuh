@@ -98,6 +98,45 @@ __device__ __forceinline__ bool ucp_project(const M3<T> &V, M3<T> &out) {
     return true;
 }
 
+// APE / AUS+UCP update of link (x, MU) at plane position i from its staple
+// sum Vb and current value u: blocking, projection (a singular V keeps u),
+// vortex-preservation test, store if accepted.
+template <class T, int NC, int MU>
+__device__ __forceinline__ void ape_finish(const ApeParams &a, const Pt &x, int i, M3<T> Vb, const M3<T> &u,
+                                           bool &reject, bool &singular) {
+    const Geo &g = a.g;
+    const T al = sizeof(T) == 4 ? T(a.alpha_f) : T(a.alpha);
+    const T w6 = al / T(6), w1 = T(1) - al;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        Vb.re[k] = fma(w1, u.re[k], w6 * Vb.re[k]);
+        Vb.im[k] = fma(w1, u.im[k], w6 * Vb.im[k]);
+    }
+    M3<T> un;
+    if (!ucp_project<T>(Vb, un)) {
+        un = u;
+        singular = true;
+    }
+    if (NC == 12) rebuild_row2(un);
+    if (a.vp) {
+        T tr_re, tr_im;
+        vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, un, tr_re, tr_im);
+        reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
+    }
+    if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, un);
+}
+
+__device__ __forceinline__ void ape_count(const ApeParams &a, bool reject, bool singular) {
+    if (a.counters) {
+        const unsigned rb = __ballot_sync(0xffffffffu, reject);
+        const unsigned sb = __ballot_sync(0xffffffffu, singular);
+        if ((threadIdx.x & 31) == 0) {
+            if (rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
+            if (sb) atomicAdd(&a.counters[1], (unsigned long long)__popc(sb));
+        }
+    }
+}
+
 // APE / AUS with unit circle projection: one thread per link of the colour
 // class (annealed, in place) or of direction MU (colour < 0, from Usrc).
 template <class T, int NC, bool RECT, int MU>
@@ -112,36 +151,32 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
         const int i = sidx(g, x);
         const T *Us = static_cast<const T *>(a.Usrc);
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
-        const T al = sizeof(T) == 4 ? T(a.alpha_f) : T(a.alpha);
-        M3<T> Vb = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
+        const M3<T> Vb = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
         const M3<T> u = load_link<T, NC>(Us, g.P, MU, i);
-        const T w6 = al / T(6), w1 = T(1) - al;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            Vb.re[k] = fma(w1, u.re[k], w6 * Vb.re[k]);
-            Vb.im[k] = fma(w1, u.im[k], w6 * Vb.im[k]);
-        }
-        M3<T> un;
-        if (!ucp_project<T>(Vb, un)) {
-            un = u;
-            singular = true;
-        }
-        if (NC == 12) rebuild_row2(un);
-        if (a.vp) {
-            T tr_re, tr_im;
-            vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, un, tr_re, tr_im);
-            reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
-        }
-        if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, un);
+        ape_finish<T, NC, MU>(a, x, i, Vb, u, reject, singular);
     }
-    if (a.counters) {
-        const unsigned rb = __ballot_sync(0xffffffffu, reject);
-        const unsigned sb = __ballot_sync(0xffffffffu, singular);
-        if ((threadIdx.x & 31) == 0) {
-            if (rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
-            if (sb) atomicAdd(&a.counters[1], (unsigned long long)__popc(sb));
-        }
+    ape_count(a, reject, singular);
+}
+
+// FP32 over-improved AUS+UCP with the link ring of k_subsweep_ring.
+template <int NC, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeParams a) {
+    __shared__ float4 ring4[kRingDepth * (NC / 4) * VS_RING_THREADS];
+    __shared__ float2 ring2[NC == 18 ? kRingDepth * VS_RING_THREADS : 1];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false, singular = false;
+    if (active) {
+        const Geo &g = a.g;
+        const Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        const int i = sidx(g, x);
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
+        M3<float> Ux;
+        const M3<float> Vb =
+            staple_sum_ring<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
+        ape_finish<float, NC, MU>(a, x, i, Vb, Ux, reject, singular);
     }
+    ape_count(a, reject, singular);
 }
 
 // One Runge-Kutta stage for every link of direction MU (thread t = plane
@@ -187,9 +222,24 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
 
 template <class T, int NC>
 cudaError_t launch_ape_tpl(bool rect, int mu, const ApeParams &p, cudaStream_t st) {
+    if (p.n_threads <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4 && VS_RING) {
+        // annealed classes only: for the simultaneous schedule (every link of
+        // mu from the previous field) the plain-load kernel measured faster
+        if (rect && p.colour >= 0) {
+            const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
+            switch (mu) {
+                case 0: k_ape_ring<NC, 0><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                case 1: k_ape_ring<NC, 1><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                case 2: k_ape_ring<NC, 2><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                default: k_ape_ring<NC, 3><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+            }
+            count_launches(1);
+            return cudaGetLastError();
+        }
+    }
     const int threads = VS_SUBSWEEP_THREADS;
     const int blocks = (p.n_threads + threads - 1) / threads;
-    if (blocks == 0) return cudaSuccess;
 #define VS_LAUNCH(R, M) k_ape<T, NC, R, M><<<blocks, threads, 0, st>>>(p)
     if (rect) {
         switch (mu) {

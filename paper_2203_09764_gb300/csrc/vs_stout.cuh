@@ -649,6 +649,17 @@ __device__ __forceinline__ M3<float> staple_sum_ring(const Geo &g, const float *
     return sig;
 }
 
+// This thread's column of the ring arrays of a kernel.
+template <int NC>
+__device__ __forceinline__ LinkRing<NC> ring_of(float4 *ring4, float2 *ring2) {
+    LinkRing<NC> R;
+    R.v4 = ring4 + threadIdx.x;
+    R.v2 = ring2 + (NC == 18 ? threadIdx.x : 0);
+    R.a4 = (uint32_t)__cvta_generic_to_shared(ring4 + threadIdx.x);
+    R.a2 = (uint32_t)__cvta_generic_to_shared(ring2 + (NC == 18 ? threadIdx.x : 0));
+    return R;
+}
+
 template <int NC, int MU>
 __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring(SubsweepParams a) {
     __shared__ float4 ring4[kRingDepth * (NC / 4) * VS_RING_THREADS];
@@ -660,11 +671,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring
         const Geo &g = a.g;
         Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
         const int i = sidx(g, x);
-        LinkRing<NC> R;
-        R.v4 = ring4 + threadIdx.x;
-        R.v2 = ring2 + (NC == 18 ? threadIdx.x : 0);
-        R.a4 = (uint32_t)__cvta_generic_to_shared(ring4 + threadIdx.x);
-        R.a2 = (uint32_t)__cvta_generic_to_shared(ring2 + (NC == 18 ? threadIdx.x : 0));
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
         M3<float> sig = staple_sum_ring<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
         stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
@@ -730,6 +737,30 @@ __device__ __forceinline__ void maxretr(M3<T> &u, const M3<T> &Vb, int n_hits) {
     }
 }
 
+// AUS update of link (x, MU) at plane position i from its staple sum Vb and
+// current value u: blocking V = (1 - alpha) u + (alpha / 6) Vb, MaxReTr,
+// vortex-preservation test, store if accepted.
+template <class T, int NC, int MU>
+__device__ __forceinline__ void aus_finish(const AusParams &a, const Pt &x, int i, M3<T> Vb, M3<T> u,
+                                           bool &reject) {
+    const Geo &g = a.g;
+    const T al = sizeof(T) == 4 ? T(a.alpha_f) : T(a.alpha);
+    const T w6 = al / T(6), w1 = T(1) - al;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        Vb.re[k] = fma(w1, u.re[k], w6 * Vb.re[k]);
+        Vb.im[k] = fma(w1, u.im[k], w6 * Vb.im[k]);
+    }
+    maxretr<T>(u, Vb, a.n_hits);
+    if (NC == 12) rebuild_row2(u);
+    if (a.vp) {
+        T tr_re, tr_im;
+        vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, u, tr_re, tr_im);
+        reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
+    }
+    if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, u);
+}
+
 template <class T, int NC, bool RECT, int MU>
 __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1)
     k_aus(AusParams a) {
@@ -740,25 +771,34 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
         const Geo &g = a.g;
         const Pt x = class_site<MU>(g, a.colour, t);
         const int i = sidx(g, x);
-        T *U = static_cast<T *>(a.U);
+        const T *U = static_cast<const T *>(a.U);
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
-        const T al = sizeof(T) == 4 ? T(a.alpha_f) : T(a.alpha);
-        M3<T> Vb = staple_sum<T, NC, RECT, MU>(g, U, x, c0, c1);
-        M3<T> u = load_link<T, NC>(U, g.P, MU, i);
-        const T w6 = al / T(6), w1 = T(1) - al;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            Vb.re[k] = fma(w1, u.re[k], w6 * Vb.re[k]);
-            Vb.im[k] = fma(w1, u.im[k], w6 * Vb.im[k]);
-        }
-        maxretr<T>(u, Vb, a.n_hits);
-        if (NC == 12) rebuild_row2(u);
-        if (a.vp) {
-            T tr_re, tr_im;
-            vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, u, tr_re, tr_im);
-            reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
-        }
-        if (!reject) store_link<T, NC>(U, g.P, MU, i, u);
+        const M3<T> Vb = staple_sum<T, NC, RECT, MU>(g, U, x, c0, c1);
+        const M3<T> u = load_link<T, NC>(U, g.P, MU, i);
+        aus_finish<T, NC, MU>(a, x, i, Vb, u, reject);
+    }
+    if (a.counters) {
+        unsigned rb = __ballot_sync(0xffffffffu, reject);
+        if ((threadIdx.x & 31) == 0 && rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
+    }
+}
+
+// FP32 over-improved AUS with the link ring of k_subsweep_ring.
+template <int NC, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_aus_ring(AusParams a) {
+    __shared__ float4 ring4[kRingDepth * (NC / 4) * VS_RING_THREADS];
+    __shared__ float2 ring2[NC == 18 ? kRingDepth * VS_RING_THREADS : 1];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false;
+    if (active) {
+        const Geo &g = a.g;
+        const Pt x = class_site<MU>(g, a.colour, t);
+        const int i = sidx(g, x);
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
+        M3<float> Ux;
+        const M3<float> Vb = staple_sum_ring<NC, MU>(g, static_cast<const float *>(a.U), x, a.c0_f, a.c1_f, R, Ux);
+        aus_finish<float, NC, MU>(a, x, i, Vb, Ux, reject);
     }
     if (a.counters) {
         unsigned rb = __ballot_sync(0xffffffffu, reject);

@@ -50,9 +50,23 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
 
 template <class T, int NC>
 cudaError_t launch_aus_tpl(bool rect, int mu, const AusParams &p, cudaStream_t st) {
+    if (p.n_threads <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4 && VS_RING) {
+        // FP32 over-improved staples: the link-ring kernel
+        if (rect) {
+            const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
+            switch (mu) {
+                case 0: k_aus_ring<NC, 0><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                case 1: k_aus_ring<NC, 1><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                case 2: k_aus_ring<NC, 2><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                default: k_aus_ring<NC, 3><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+            }
+            count_launches(1);
+            return cudaGetLastError();
+        }
+    }
     const int threads = VS_SUBSWEEP_THREADS;
     const int blocks = (p.n_threads + threads - 1) / threads;
-    if (blocks == 0) return cudaSuccess;
 #define VS_LAUNCH(R, M) k_aus<T, NC, R, M><<<blocks, threads, 0, st>>>(p)
     if (rect) {
         switch (mu) {
