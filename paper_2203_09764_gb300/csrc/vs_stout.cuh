@@ -403,6 +403,11 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
 #ifndef VS_RING_MINB
 #define VS_RING_MINB (384 / VS_RING_THREADS)
 #endif
+// depth of the link ring of the stout class kernel: 8 (74 KB of dynamic shared
+// memory per 128-thread block) or 4 (the AUS / APE kernels always use 4)
+#ifndef VS_RING_DEPTH
+#define VS_RING_DEPTH 8
+#endif
 
 constexpr int kRingDepth = 4;   // the stream patterns below assume 4
 
@@ -438,9 +443,8 @@ __device__ __forceinline__ void ring_skip() { asm volatile("cp.async.commit_grou
 // Wait for the link in slot SLOT (all but the kRingDepth - 1 newest groups
 // are complete) and read it, daggered if DAG.
 template <int NC, bool DAG, int SLOT>
-__device__ __forceinline__ M3<float> ring_take(const LinkRing<NC> &R) {
+__device__ __forceinline__ M3<float> ring_read(const LinkRing<NC> &R) {
     constexpr int NQ = NC / 4;
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRingDepth - 1) : "memory");
     M3<float> m;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -453,6 +457,12 @@ __device__ __forceinline__ M3<float> ring_take(const LinkRing<NC> &R) {
     }
     if (NC == 12) rebuild_row2(m);
     return DAG ? m3_dag(m) : m;
+}
+
+template <int NC, bool DAG, int SLOT>
+__device__ __forceinline__ M3<float> ring_take(const LinkRing<NC> &R) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRingDepth - 1) : "memory");
+    return ring_read<NC, DAG, SLOT>(R);
 }
 
 // Plane-position shifts along mu of the anchor of F: b0, b1, b2 are the
@@ -649,6 +659,204 @@ __device__ __forceinline__ M3<float> staple_sum_ring(const Geo &g, const float *
     return sig;
 }
 
+// ---------------------------------------------------------------------------
+// Depth-8 ring: the same stream with 8 links in flight per thread.  Staple
+// units are padded to 8 stream entries (6 links, 2 empty commit groups), so
+// every slot is the stream index modulo 8 and known at compile time: F units
+// use slots 4 sigma + K (sigma = 1 for s = -1), staple units slots K, U_mu(x)
+// (entry 96) slot 0.  A refill targets the entry 8 ahead: for F units the
+// same (s, K) at the next nu; for staple units (nu, -s) or the next nu.
+// ---------------------------------------------------------------------------
+
+template <int NC, bool DAG, int SLOT>
+__device__ __forceinline__ M3<float> ring_take8(const LinkRing<NC> &R) {
+    asm volatile("cp.async.wait_group 7;\n" ::: "memory");
+    return ring_read<NC, DAG, SLOT>(R);
+}
+
+// ring_fetch with a predicate: on == false commits an empty group.
+template <int NC, int SLOT>
+__device__ __forceinline__ void ring_fetch_if(const LinkRing<NC> &R, const float *base, long long P, int i,
+                                              bool on) {
+    constexpr int NQ = NC / 4;
+    const int pr = on ? 1 : 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float4 *src = reinterpret_cast<const float4 *>(base + 4 * q * P) + i;
+        const uint32_t dst = R.a4 + (uint32_t)((SLOT * NQ + q) * VS_RING_THREADS * 16);
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
+            " @p cp.async.cg.shared.global [%0], [%1], 16;\n}\n" ::"r"(dst), "l"(src), "r"(pr)
+            : "memory");
+    }
+    if (NC == 18) {
+        const float2 *src = reinterpret_cast<const float2 *>(base + 16 * P) + i;
+        const uint32_t dst = R.a2 + (uint32_t)(SLOT * VS_RING_THREADS * 8);
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
+            " @p cp.async.ca.shared.global [%0], [%1], 8;\n}\n" ::"r"(dst), "l"(src), "r"(pr)
+            : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Refill after F link K of unit (nu, s): the same link of the next nu (An,
+// mnext); after the last nu of F(x - mu) (to_staples) the staple entry
+// 4 sigma + K of the first staple unit (s = +1), empty for the padding.
+template <int NC, int S, int K>
+__device__ __forceinline__ void f_refill8(const LinkRing<NC> &R, const float *Umu, const float *Un, long long P,
+                                          const Around &An, const MuOff &mnext, bool to_staples) {
+    constexpr int SL = (S < 0 ? 4 : 0) + K;
+    const float *base, *bt;
+    int pos, pt;
+    f_link<S, K>(An, mnext, Umu, Un, base, pos);
+    constexpr int TK = (S < 0 ? 4 : 0) + K;     // staple entry
+    if constexpr (TK <= 5) {
+        t_link<1, (TK <= 5 ? TK : 0)>(An, Umu, Un, bt, pt);
+        ring_fetch<NC, SL>(R, to_staples ? bt : base, P, to_staples ? pt : pos);
+    } else {
+        ring_fetch_if<NC, SL>(R, base, P, pos, !to_staples);
+    }
+}
+
+template <int NC, int S>
+__device__ __forceinline__ void f_unit8(const LinkRing<NC> &R, M3<float> &F, const float *Umu, const float *Un,
+                                        long long P, const Around &An, const MuOff &mnext, bool to_staples) {
+    constexpr int B0 = S < 0 ? 4 : 0;
+    M3<float> L0 = ring_take8<NC, (S < 0), B0 + 0>(R);
+    f_refill8<NC, S, 0>(R, Umu, Un, P, An, mnext, to_staples);
+    M3<float> L1 = ring_take8<NC, false, B0 + 1>(R);
+    f_refill8<NC, S, 1>(R, Umu, Un, P, An, mnext, to_staples);
+    M3<float> W = m3_mul(L0, L1);
+    M3<float> L2 = ring_take8<NC, false, B0 + 2>(R);
+    f_refill8<NC, S, 2>(R, Umu, Un, P, An, mnext, to_staples);
+    W = m3_mul(W, L2);
+    M3<float> L3 = ring_take8<NC, (S > 0), B0 + 3>(R);
+    f_refill8<NC, S, 3>(R, Umu, Un, P, An, mnext, to_staples);
+    m3_madd(F, W, L3);
+}
+
+// Refill after staple link K of unit (nu, s): s = +1 -> (nu, -1) on A;
+// s = -1 -> (next nu, +1) on An, or after the last nu U_mu(x) (K = 0) and
+// nothing else.
+template <int NC, int S, int K>
+__device__ __forceinline__ void t_refill8(const LinkRing<NC> &R, const float *Umu, const float *Unu,
+                                          const float *Un, long long P, const Around &A, const Around &An,
+                                          bool last) {
+    const float *base;
+    int pos;
+    if constexpr (S > 0) {
+        t_link<-1, K>(A, Umu, Unu, base, pos);
+        ring_fetch<NC, K>(R, base, P, pos);
+    } else {
+        t_link<1, K>(An, Umu, Un, base, pos);
+        if constexpr (K == 0) {
+            ring_fetch<NC, K>(R, last ? Umu : base, P, last ? A.i0 : pos);
+        } else {
+            ring_fetch_if<NC, K>(R, base, P, pos, !last);
+        }
+    }
+}
+
+template <int NC, int S>
+__device__ __forceinline__ void t_unit8(const LinkRing<NC> &R, M3<float> &sig, float c0, float c1,
+                                        const float *Umu, const float *Unu, const float *Un, long long P,
+                                        const Around &A, const Around &An, bool last) {
+    M3<float> T0 = ring_take8<NC, (S < 0), 0>(R);
+    t_refill8<NC, S, 0>(R, Umu, Unu, Un, P, A, An, last);
+    M3<float> T1 = ring_take8<NC, false, 1>(R);
+    t_refill8<NC, S, 1>(R, Umu, Unu, Un, P, A, An, last);
+    M3<float> Tt = m3_mul(T0, T1);
+    M3<float> T2 = ring_take8<NC, (S > 0), 2>(R);
+    t_refill8<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
+    Tt = m3_mul(Tt, T2);
+    M3<float> N = ring_take8<NC, false, 3>(R);
+    t_refill8<NC, S, 3>(R, Umu, Unu, Un, P, A, An, last);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        N.re[k] = fmaf(c1, Tt.re[k], c0 * N.re[k]);
+        N.im[k] = fmaf(c1, Tt.im[k], c0 * N.im[k]);
+    }
+    M3<float> Af = ring_take8<NC, (S < 0), 4>(R);
+    t_refill8<NC, S, 4>(R, Umu, Unu, Un, P, A, An, last);
+    M3<float> AN = m3_mul(Af, N);
+    M3<float> C = ring_take8<NC, (S > 0), 5>(R);
+    t_refill8<NC, S, 5>(R, Umu, Unu, Un, P, A, An, last);
+    m3_madd(sig, AN, C);
+    ring_skip();     // padding entries 6, 7: their refills are padding too
+    ring_skip();
+}
+
+template <int NC, int MU>
+__device__ __forceinline__ M3<float> staple_sum_ring8(const Geo &g, const float *__restrict__ U, Pt x, float c0,
+                                                      float c1, const LinkRing<NC> &R, M3<float> &Ux) {
+    const long long P = g.P;
+    Around A, An;
+    A.i0 = sidx(g, x);
+    A.dmm1 = shift_delta(g, x, MU, -1);
+    A.dmp1 = shift_delta(g, x, MU, 1);
+    A.dmp2 = shift_delta(g, x, MU, 2);
+    An = A;
+    const MuOff m_x = {0, A.dmp1, A.dmp2}, m_xm = {A.dmm1, 0, A.dmp1};
+    const float *Umu = U + (long long)MU * NC * P;
+    const int nu1 = (MU + 1) & 3;
+    around_nu(g, x, nu1, true, A);
+    const float *Unu = U + (long long)nu1 * NC * P;
+    {   // prologue: both units of the first nu of F(x) into slots 0-7
+        const float *b;
+        int q;
+        f_link<1, 0>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 0>(R, b, P, q);
+        f_link<1, 1>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 1>(R, b, P, q);
+        f_link<1, 2>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 2>(R, b, P, q);
+        f_link<1, 3>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 3>(R, b, P, q);
+        f_link<-1, 0>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 4>(R, b, P, q);
+        f_link<-1, 1>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 5>(R, b, P, q);
+        f_link<-1, 2>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 6>(R, b, P, q);
+        f_link<-1, 3>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 7>(R, b, P, q);
+    }
+    M3<float> sig;
+    m3_zero(sig);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const MuOff m = h ? m_xm : m_x;
+        const M3<float> Lc = load_link<float, NC>(U, P, MU, A.i0 + (h ? A.dmm1 : A.dmp1));
+        M3<float> F;
+        m3_zero(F);
+#pragma unroll 1
+        for (int j = 1; j < 4; ++j) {
+            const bool last = j == 3;
+            const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
+            around_nu(g, x, nun, true, An);
+            const float *Un = U + (long long)nun * NC * P;
+            const MuOff mn = last ? m_xm : m;
+            f_unit8<NC, 1>(R, F, Umu, Un, P, An, mn, last && h == 1);
+            f_unit8<NC, -1>(R, F, Umu, Un, P, An, mn, last && h == 1);
+            A = An;
+            Unu = Un;
+        }
+        M3<float> t = h ? m3_mul_dn(Lc, F) : m3_mul_nd(F, Lc);
+        m3_axpy(sig, c1, t);
+    }
+#pragma unroll 1
+    for (int j = 1; j < 4; ++j) {
+        const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
+        around_nu(g, x, nun, true, An);
+        const float *Un = U + (long long)nun * NC * P;
+        t_unit8<NC, 1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
+        t_unit8<NC, -1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
+        A = An;
+        Unu = Un;
+    }
+    Ux = ring_take8<NC, false, 0>(R);
+    return sig;
+}
+
+// bytes of dynamic shared memory of the depth-8 ring kernels
+template <int NC>
+constexpr int ring8_smem_bytes() {
+    return 8 * VS_RING_THREADS * ((NC / 4) * 16 + (NC == 18 ? 8 : 0));
+}
+
 // This thread's column of the ring arrays of a kernel.
 template <int NC>
 __device__ __forceinline__ LinkRing<NC> ring_of(float4 *ring4, float2 *ring2) {
@@ -658,6 +866,26 @@ __device__ __forceinline__ LinkRing<NC> ring_of(float4 *ring4, float2 *ring2) {
     R.a4 = (uint32_t)__cvta_generic_to_shared(ring4 + threadIdx.x);
     R.a2 = (uint32_t)__cvta_generic_to_shared(ring2 + (NC == 18 ? threadIdx.x : 0));
     return R;
+}
+
+template <int NC, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring8(SubsweepParams a) {
+    extern __shared__ float4 ring8_dyn[];
+    float4 *ring4 = ring8_dyn;
+    float2 *ring2 = reinterpret_cast<float2 *>(ring8_dyn + 8 * (NC / 4) * VS_RING_THREADS);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false, used64 = false;
+    if (active) {
+        const Geo &g = a.g;
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        const int i = sidx(g, x);
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
+        M3<float> Ux;
+        M3<float> sig = staple_sum_ring8<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
+        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
+    }
+    count_update(a, reject, used64);
 }
 
 template <int NC, int MU>
