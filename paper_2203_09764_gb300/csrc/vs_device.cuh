@@ -191,6 +191,55 @@ __device__ __forceinline__ void m3_mul_f32(M3<float> &r, const M3<float> &a, con
     }
 }
 
+// rows 0-1 of r = a * b (rows 0-1 of a, all of b); row 2 of r is not written.
+__device__ __forceinline__ void m3_mul_2r(M3<float> &r, const M3<float> &a, const M3<float> &b) {
+#if VS_FFMA2
+    f2pk bb[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) bb[e] = pk2(b.re[e], b.im[e]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        f2pk P[3], Q[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { P[j] = pk2(0.f, 0.f); Q[j] = pk2(0.f, 0.f); }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const f2pk ar = pk2(a.re[i * 3 + k], a.re[i * 3 + k]);
+            const f2pk ai = pk2(a.im[i * 3 + k], a.im[i * 3 + k]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                P[j] = fma2(ar, bb[k * 3 + j], P[j]);
+                Q[j] = fma2(ai, bb[k * 3 + j], Q[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float px, py, qx, qy;
+            upk2(P[j], px, py);
+            upk2(Q[j], qx, qy);
+            r.re[i * 3 + j] = px - qy;
+            r.im[i * 3 + j] = py + qx;
+        }
+    }
+#else
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sr = fmaf(a.re[i * 3 + k], b.re[k * 3 + j], sr);
+                sr = fmaf(-a.im[i * 3 + k], b.im[k * 3 + j], sr);
+                si = fmaf(a.re[i * 3 + k], b.im[k * 3 + j], si);
+                si = fmaf(a.im[i * 3 + k], b.re[k * 3 + j], si);
+            }
+            r.re[i * 3 + j] = sr;
+            r.im[i * 3 + j] = si;
+        }
+#endif
+}
+
 // r = a * b.  FP64: every entry is the same chain of fused multiply-adds
 // started from zero; FP32: m3_mul_f32.  Either way entries built from equal
 // inputs come out bit-identical.
