@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
 template <class T, int NC>
 cudaError_t launch_ape_tpl(bool rect, int mu, const ApeParams &p, cudaStream_t st) {
     if (p.n_threads <= 0) return cudaSuccess;
-    if constexpr (sizeof(T) == 4 && VS_RING && !VS_RING_LOCK) {
+    if constexpr (sizeof(T) == 4 && VS_RING) {
         // annealed classes only: for the simultaneous schedule (every link of
         // mu from the previous field) the plain-load kernel measured faster
         if (rect && p.colour >= 0) {

@@ -409,6 +409,11 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
 #define VS_RING_DEPTH 8
 #endif
 
+// VS_TWO_ROW: chains of SU(3) links form only rows 0-1 of each partial product
+#ifndef VS_TWO_ROW
+#define VS_TWO_ROW 1
+#endif
+
 constexpr int kRingDepth = 4;   // the stream patterns below assume 4
 
 template <int NC>
@@ -461,10 +466,10 @@ __device__ __forceinline__ M3<float> ring_read(const LinkRing<NC> &R) {
     return DAG ? m3_dag(m) : m;
 }
 
-template <int NC, bool DAG, int SLOT>
+template <int NC, bool DAG, int SLOT, bool FULL = true>
 __device__ __forceinline__ M3<float> ring_take(const LinkRing<NC> &R) {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kRingDepth - 1) : "memory");
-    return ring_read<NC, DAG, SLOT>(R);
+    return ring_read<NC, DAG, SLOT, FULL>(R);
 }
 
 // Plane-position shifts along mu of the anchor of F: b0, b1, b2 are the
@@ -529,17 +534,31 @@ template <int NC, int S>
 __device__ __forceinline__ void f_unit(const LinkRing<NC> &R, M3<float> &F, const float *Umu, const float *Unu,
                                        const float *Un, long long P, const Around &A, const Around &An,
                                        const MuOff &m, const MuOff &mnext, bool to_staples) {
-    M3<float> L0 = ring_take<NC, (S < 0), 0>(R);
+    M3<float> L0 = ring_take<NC, (S < 0), 0, !VS_TWO_ROW>(R);
     f_refill<NC, S, 0>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
     M3<float> L1 = ring_take<NC, false, 1>(R);
     f_refill<NC, S, 1>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-    M3<float> W = m3_mul(L0, L1);
-    M3<float> L2 = ring_take<NC, false, 2>(R);
-    f_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-    W = m3_mul(W, L2);
-    M3<float> L3 = ring_take<NC, (S > 0), 3>(R);
-    f_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-    m3_madd(F, W, L3);
+    if constexpr (VS_TWO_ROW) {
+        M3<float> W, W2, Y;
+        m3_mul_2r(W, L0, L1);
+        M3<float> L2 = ring_take<NC, false, 2>(R);
+        f_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+        m3_mul_2r(W2, W, L2);
+        M3<float> L3 = ring_take<NC, (S > 0), 3>(R);
+        f_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+        m3_mul_2r(Y, W2, L3);
+        rebuild_row2(Y);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { F.re[k] += Y.re[k]; F.im[k] += Y.im[k]; }
+    } else {
+        M3<float> W = m3_mul(L0, L1);
+        M3<float> L2 = ring_take<NC, false, 2>(R);
+        f_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+        W = m3_mul(W, L2);
+        M3<float> L3 = ring_take<NC, (S > 0), 3>(R);
+        f_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
+        m3_madd(F, W, L3);
+    }
 }
 
 // Refill after link K of staple unit (nu, s): 4 places ahead in units of 6.
@@ -576,14 +595,24 @@ template <int NC, int S>
 __device__ __forceinline__ void t_unit(const LinkRing<NC> &R, M3<float> &sig, float c0, float c1,
                                        const float *Umu, const float *Unu, const float *Un, long long P,
                                        const Around &A, const Around &An, bool last) {
-    M3<float> T0 = ring_take<NC, (S < 0), TSlot<S, 0>::v>(R);
+    M3<float> T0 = ring_take<NC, (S < 0), TSlot<S, 0>::v, !VS_TWO_ROW>(R);
     t_refill<NC, S, 0>(R, Umu, Unu, Un, P, A, An, last);
     M3<float> T1 = ring_take<NC, false, TSlot<S, 1>::v>(R);
     t_refill<NC, S, 1>(R, Umu, Unu, Un, P, A, An, last);
-    M3<float> Tt = m3_mul(T0, T1);
-    M3<float> T2 = ring_take<NC, (S > 0), TSlot<S, 2>::v>(R);
-    t_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
-    Tt = m3_mul(Tt, T2);
+    M3<float> Tt;
+    if constexpr (VS_TWO_ROW) {
+        M3<float> T01;
+        m3_mul_2r(T01, T0, T1);
+        M3<float> T2 = ring_take<NC, (S > 0), TSlot<S, 2>::v>(R);
+        t_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
+        m3_mul_2r(Tt, T01, T2);
+        rebuild_row2(Tt);
+    } else {
+        Tt = m3_mul(T0, T1);
+        M3<float> T2 = ring_take<NC, (S > 0), TSlot<S, 2>::v>(R);
+        t_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
+        Tt = m3_mul(Tt, T2);
+    }
     M3<float> N = ring_take<NC, false, TSlot<S, 3>::v>(R);
     t_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, last);
 #pragma unroll
@@ -676,9 +705,6 @@ __device__ __forceinline__ M3<float> ring_take8(const LinkRing<NC> &R) {
     return ring_read<NC, DAG, SLOT, FULL>(R);
 }
 
-#ifndef VS_TWO_ROW
-#define VS_TWO_ROW 1
-#endif
 
 // ring_fetch with a predicate: on == false commits an empty group.
 template <int NC, int SLOT>
@@ -826,10 +852,7 @@ __device__ __forceinline__ void t_unit8(const LinkRing<NC> &R, M3<float> &sig, f
     ring_skip();
 }
 
-// LOCK: every thread of the block runs the whole stream and a block barrier
-// separates the passes, so all warps of an SM execute the same pass (its code
-// alone is then the instruction working set).
-template <int NC, int MU, bool LOCK>
+template <int NC, int MU>
 __device__ __forceinline__ M3<float> staple_sum_ring8(const Geo &g, const float *__restrict__ U, Pt x, float c0,
                                                       float c1, const LinkRing<NC> &R, M3<float> &Ux) {
     const long long P = g.P;
@@ -878,7 +901,6 @@ __device__ __forceinline__ M3<float> staple_sum_ring8(const Geo &g, const float 
         }
         M3<float> t = h ? m3_mul_dn(Lc, F) : m3_mul_nd(F, Lc);
         m3_axpy(sig, c1, t);
-        if (LOCK) __syncthreads();
     }
 #pragma unroll 1
     for (int j = 1; j < 4; ++j) {
@@ -891,7 +913,6 @@ __device__ __forceinline__ M3<float> staple_sum_ring8(const Geo &g, const float 
         Unu = Un;
     }
     Ux = ring_take8<NC, false, 0>(R);
-    if (LOCK) __syncthreads();
     return sig;
 }
 
@@ -912,10 +933,6 @@ __device__ __forceinline__ LinkRing<NC> ring_of(float4 *ring4, float2 *ring2) {
     return R;
 }
 
-#ifndef VS_RING_LOCK
-#define VS_RING_LOCK 0
-#endif
-
 template <int NC, int MU>
 __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring8(SubsweepParams a) {
     extern __shared__ float4 ring8_dyn[];
@@ -924,18 +941,14 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
     bool reject = false, used64 = false;
-    if (VS_RING_LOCK || active) {
-        // with the block barriers every thread runs the stream; threads past
-        // the end repeat the last site and store nothing
-        const int tt = active ? t : a.n_threads - 1;
+    if (active) {
         const Geo &g = a.g;
-        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, tt) : site_of_index(g, tt);
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
         const int i = sidx(g, x);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
-        M3<float> sig = staple_sum_ring8<NC, MU, VS_RING_LOCK != 0>(g, static_cast<const float *>(a.Usrc), x,
-                                                                     a.c0_f, a.c1_f, R, Ux);
-        if (active) stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
+        M3<float> sig = staple_sum_ring8<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
+        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
     }
     count_update(a, reject, used64);
 }

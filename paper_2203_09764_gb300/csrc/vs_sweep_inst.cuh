@@ -69,7 +69,7 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
 template <class T, int NC>
 cudaError_t launch_aus_tpl(bool rect, int mu, const AusParams &p, cudaStream_t st) {
     if (p.n_threads <= 0) return cudaSuccess;
-    if constexpr (sizeof(T) == 4 && VS_RING && !VS_RING_LOCK) {
+    if constexpr (sizeof(T) == 4 && VS_RING) {
         // FP32 over-improved staples: the link-ring kernel
         if (rect) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
