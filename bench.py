@@ -39,8 +39,8 @@ REUNIT = 10
 BYTES_PER_UPDATE = {(1, 18): 17 * 72 + 1, (1, 12): 17 * 48 + 1, (0, 18): 17 * 144 + 1}
 FLOPS_PER_UPDATE_OVERIMPROVED = 65 * 216 + 600
 # DRAM bytes (read + write) of one class-update launch of this kernel version,
-# from `ncu --set full` on the same command (profiles/k_subsweep_ring_f32_*.md)
-NCU_TRAFFIC_PER_LAUNCH = 709.504512e6 + 35.991808e6
+# from `ncu --set full` on the same command (profiles/k_subsweep_f32_*.md)
+NCU_TRAFFIC_PER_LAUNCH = 647.734016e6 + 43.077888e6
 # FP32 FMA peak of the GPU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -253,7 +253,7 @@ def run_ours(args):
     bpu = BYTES_PER_UPDATE[(1, 18)]
     achieved = units * bpu / (per_launch_ms / 1e3) / 1e9
     tflops = units * FLOPS_PER_UPDATE_OVERIMPROVED / (per_launch_ms / 1e3) / 1e12
-    line["roofline"] = {"kernel": "k_subsweep_ring8<18,mu> (FP32 over-improved class update)", "bound": "hbm",
+    line["roofline"] = {"kernel": "k_subsweep_fused<18,mu> (FP32 over-improved class update)", "bound": "hbm",
                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_PER_LAUNCH,
                         "peak_source": src, "per_launch_ms": per_launch_ms,

@@ -408,6 +408,10 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
 #ifndef VS_RING_DEPTH
 #define VS_RING_DEPTH 8
 #endif
+// VS_FUSED: the stout class kernel reads every link of a (nu, s) unit once
+#ifndef VS_FUSED
+#define VS_FUSED 1
+#endif
 
 // VS_TWO_ROW: chains of SU(3) links form only rows 0-1 of each partial product
 #ifndef VS_TWO_ROW
@@ -922,6 +926,183 @@ constexpr int ring8_smem_bytes() {
     return 8 * VS_RING_THREADS * ((NC / 4) * 16 + (NC == 18 ? 8 : 0));
 }
 
+// ---------------------------------------------------------------------------
+// One pass per (nu, s), every link read once.  With A = step(x, s nu),
+// B = U_mu(x+s nu), C = step(x+s nu+mu, -s nu), the wide backward rectangle,
+// the plaquette staple and the tall rectangle of (nu, s) all end in C:
+//   Sigma = c1 F(x) U_mu^dag(x+mu)
+//         + sum_{nu,s} [c1 U_mu^dag(x-mu) G H B + c0 A B + c1 A T] C,
+// G = step(x-mu, s nu), H = U_mu(x-mu+s nu), T the upper half of the tall
+// rectangle, and F(x) = sum A B D E (D = U_mu(x+s nu+mu), E = step(x+s nu+2mu,
+// -s nu)) shares A B.  A unit reads its 10 distinct links once (63 per update
+// with U_mu(x +- mu) and U_mu(x), against 85 + 2 in three passes), in a
+// 12-entry stream slot pattern: A B G H D E T0 T1 T2 C, then two spare
+// entries that carry U_mu^dag(x+mu) and U_mu(x) in the last unit.  Ring depth 6
+// (slot = entry mod 6, compile-time).
+// ---------------------------------------------------------------------------
+
+template <int NC, bool DAG, int SLOT, bool FULL = true>
+__device__ __forceinline__ M3<float> ring_take6(const LinkRing<NC> &R) {
+    asm volatile("cp.async.wait_group 5;\n" ::: "memory");
+    return ring_read<NC, DAG, SLOT, FULL>(R);
+}
+
+// Link K of the unit (nu, s): direction and site x + a nu + b mu.
+template <int S, int K>
+__device__ __forceinline__ void u_link(const Around &A, const float *Umu, const float *Unu, const float *&base,
+                                       int &pos) {
+    constexpr int f0 = S > 0 ? 0 : -1, f1 = S > 0 ? 1 : -2;
+    constexpr bool mu = K == 1 || K == 3 || K == 4 || K == 7;
+    constexpr int a = K == 0 ? f0 : K == 1 ? S : K == 2 ? f0 : K == 3 ? S : K == 4 ? S : K == 5 ? f0
+                    : K == 6 ? f1 : K == 7 ? 2 * S : K == 8 ? f1 : f0;
+    constexpr int b = K == 0 ? 0 : K == 1 ? 0 : K == 2 ? -1 : K == 3 ? -1 : K == 4 ? 1 : K == 5 ? 2
+                    : K == 6 ? 0 : K == 7 ? 0 : K == 8 ? 1 : 1;
+    base = mu ? Umu : Unu;
+    pos = around_pos(A, a, b);
+}
+
+// Refill after entry K of unit (nu, s), into slot K mod 6: entry K + 6 of the
+// same unit (the spare entries 10, 11 carry U_mu(x+mu), U_mu(x) in the last
+// unit, nothing otherwise), or entry K - 6 of the next unit: (nu, -1) for
+// s = +1, (next nu, +1) on An for s = -1, nothing after the last.
+template <int NC, int S, int K>
+__device__ __forceinline__ void u_refill(const LinkRing<NC> &R, const float *Umu, const float *Unu,
+                                         const float *Un, long long P, const Around &A, const Around &An,
+                                         bool last) {
+    constexpr int SL = K % 6;
+    const float *base;
+    int pos;
+    if constexpr (K + 6 <= 9) {
+        u_link<S, (K + 6 <= 9 ? K + 6 : 0)>(A, Umu, Unu, base, pos);
+        ring_fetch<NC, SL>(R, base, P, pos);
+    } else if constexpr (K + 6 <= 11) {
+        // spare entries: U_mu(x+mu) (K + 6 = 10) and U_mu(x) (11) in the last unit
+        const int p = K + 6 == 10 ? A.i0 + A.dmp1 : A.i0;
+        if constexpr (S > 0) ring_skip();
+        else ring_fetch_if<NC, SL>(R, Umu, P, p, last);
+    } else if constexpr (S > 0) {
+        u_link<-1, (K >= 6 ? K - 6 : 0)>(A, Umu, Unu, base, pos);
+        ring_fetch<NC, SL>(R, base, P, pos);
+    } else {
+        u_link<1, (K >= 6 ? K - 6 : 0)>(An, Umu, Un, base, pos);
+        ring_fetch_if<NC, SL>(R, base, P, pos, !last);
+    }
+}
+
+template <int NC, int S>
+__device__ __forceinline__ void fused_unit(const LinkRing<NC> &R, M3<float> &Facc, M3<float> &sig, float c0,
+                                           float c1, const M3<float> &Lm, const float *Umu, const float *Unu,
+                                           const float *Un, long long P, const Around &A, const Around &An,
+                                           bool last) {
+    const M3<float> Af = ring_take6<NC, (S < 0), 0, false>(R);
+    u_refill<NC, S, 0>(R, Umu, Unu, Un, P, A, An, last);
+    const M3<float> B = ring_take6<NC, false, 1>(R);
+    u_refill<NC, S, 1>(R, Umu, Unu, Un, P, A, An, last);
+    M3<float> AB;
+    m3_mul_2r(AB, Af, B);
+    M3<float> X, Y;
+    {   // c1 U_mu^dag(x-mu) G H B
+        const M3<float> G = ring_take6<NC, (S < 0), 2>(R);
+        u_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
+        m3_mul_2r(X, Lm, G);
+        const M3<float> H = ring_take6<NC, false, 3>(R);
+        u_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, last);
+        m3_mul_2r(Y, X, H);
+        m3_mul_2r(X, Y, B);
+    }
+    M3<float> W1 = X;
+    rebuild_row2(W1);
+    {   // F(x) += A B D E
+        const M3<float> D = ring_take6<NC, false, 4>(R);
+        u_refill<NC, S, 4>(R, Umu, Unu, Un, P, A, An, last);
+        m3_mul_2r(X, AB, D);
+        const M3<float> E = ring_take6<NC, (S > 0), 5>(R);
+        u_refill<NC, S, 5>(R, Umu, Unu, Un, P, A, An, last);
+        m3_mul_2r(Y, X, E);
+        rebuild_row2(Y);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { Facc.re[k] += Y.re[k]; Facc.im[k] += Y.im[k]; }
+    }
+    {   // A T, T = T0 T1 T2
+        const M3<float> T0 = ring_take6<NC, (S < 0), 0, false>(R);
+        u_refill<NC, S, 6>(R, Umu, Unu, Un, P, A, An, last);
+        const M3<float> T1 = ring_take6<NC, false, 1>(R);
+        u_refill<NC, S, 7>(R, Umu, Unu, Un, P, A, An, last);
+        m3_mul_2r(X, T0, T1);
+        const M3<float> T2 = ring_take6<NC, (S > 0), 2>(R);
+        u_refill<NC, S, 8>(R, Umu, Unu, Un, P, A, An, last);
+        m3_mul_2r(Y, X, T2);
+        rebuild_row2(Y);
+        m3_mul_2r(X, Af, Y);
+        rebuild_row2(X);
+    }
+    rebuild_row2(AB);
+    // Yc = c1 (W1 + A T) + c0 A B
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        Y.re[k] = fmaf(c0, AB.re[k], c1 * (W1.re[k] + X.re[k]));
+        Y.im[k] = fmaf(c0, AB.im[k], c1 * (W1.im[k] + X.im[k]));
+    }
+    const M3<float> C = ring_take6<NC, (S > 0), 3>(R);
+    u_refill<NC, S, 9>(R, Umu, Unu, Un, P, A, An, last);
+    m3_madd(sig, Y, C);
+    u_refill<NC, S, 10>(R, Umu, Unu, Un, P, A, An, last);   // spare entries: refills only
+    u_refill<NC, S, 11>(R, Umu, Unu, Un, P, A, An, last);
+}
+
+template <int NC, int MU>
+__device__ __forceinline__ M3<float> staple_sum_fused(const Geo &g, const float *__restrict__ U, Pt x, float c0,
+                                                      float c1, const LinkRing<NC> &R, M3<float> &Ux) {
+    const long long P = g.P;
+    Around A, An;
+    A.i0 = sidx(g, x);
+    A.dmm1 = shift_delta(g, x, MU, -1);
+    A.dmp1 = shift_delta(g, x, MU, 1);
+    A.dmp2 = shift_delta(g, x, MU, 2);
+    An = A;
+    const float *Umu = U + (long long)MU * NC * P;
+    const int nu1 = (MU + 1) & 3;
+    around_nu(g, x, nu1, true, A);
+    const float *Unu = U + (long long)nu1 * NC * P;
+    {   // prologue: entries 0-5 of the first unit
+        const float *b;
+        int q;
+        u_link<1, 0>(A, Umu, Unu, b, q); ring_fetch<NC, 0>(R, b, P, q);
+        u_link<1, 1>(A, Umu, Unu, b, q); ring_fetch<NC, 1>(R, b, P, q);
+        u_link<1, 2>(A, Umu, Unu, b, q); ring_fetch<NC, 2>(R, b, P, q);
+        u_link<1, 3>(A, Umu, Unu, b, q); ring_fetch<NC, 3>(R, b, P, q);
+        u_link<1, 4>(A, Umu, Unu, b, q); ring_fetch<NC, 4>(R, b, P, q);
+        u_link<1, 5>(A, Umu, Unu, b, q); ring_fetch<NC, 5>(R, b, P, q);
+    }
+    // U_mu^dag(x - mu): rows 0-1 only are used (left factor of two-row products)
+    const M3<float> Lm = m3_dag(load_link<float, NC>(U, P, MU, A.i0 + A.dmm1));
+    M3<float> Facc, sig;
+    m3_zero(Facc);
+    m3_zero(sig);
+#pragma unroll 1
+    for (int j = 1; j < 4; ++j) {
+        const bool last = j == 3;
+        const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
+        around_nu(g, x, nun, true, An);
+        const float *Un = U + (long long)nun * NC * P;
+        fused_unit<NC, 1>(R, Facc, sig, c0, c1, Lm, Umu, Unu, Un, P, A, An, last);
+        fused_unit<NC, -1>(R, Facc, sig, c0, c1, Lm, Umu, Unu, Un, P, A, An, last);
+        A = An;
+        Unu = Un;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    const M3<float> Lp = ring_read<NC, false, 4>(R);     // U_mu(x + mu), entry 10 of the last unit
+    Ux = ring_read<NC, false, 5>(R);                     // U_mu(x), entry 11
+    M3<float> t = m3_mul_nd(Facc, Lp);
+    m3_axpy(sig, c1, t);
+    return sig;
+}
+
+template <int NC>
+constexpr int ring6_smem_bytes() {
+    return 6 * VS_RING_THREADS * ((NC / 4) * 16 + (NC == 18 ? 8 : 0));
+}
+
 // This thread's column of the ring arrays of a kernel.
 template <int NC>
 __device__ __forceinline__ LinkRing<NC> ring_of(float4 *ring4, float2 *ring2) {
@@ -931,6 +1112,26 @@ __device__ __forceinline__ LinkRing<NC> ring_of(float4 *ring4, float2 *ring2) {
     R.a4 = (uint32_t)__cvta_generic_to_shared(ring4 + threadIdx.x);
     R.a2 = (uint32_t)__cvta_generic_to_shared(ring2 + (NC == 18 ? threadIdx.x : 0));
     return R;
+}
+
+template <int NC, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_fused(SubsweepParams a) {
+    extern __shared__ float4 ring6_dyn[];
+    float4 *ring4 = ring6_dyn;
+    float2 *ring2 = reinterpret_cast<float2 *>(ring6_dyn + 6 * (NC / 4) * VS_RING_THREADS);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false, used64 = false;
+    if (active) {
+        const Geo &g = a.g;
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        const int i = sidx(g, x);
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
+        M3<float> Ux;
+        M3<float> sig = staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
+        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
+    }
+    count_update(a, reject, used64);
 }
 
 template <int NC, int MU>

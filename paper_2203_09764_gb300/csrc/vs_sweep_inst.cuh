@@ -15,7 +15,23 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
         // FP32 over-improved staples: the cp.async link-ring kernel
         if (rect) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
-#if VS_RING_DEPTH == 8
+#if VS_FUSED
+            constexpr int sm = ring6_smem_bytes<NC>();
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_subsweep_fused<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_subsweep_fused<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_subsweep_fused<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_subsweep_fused<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                attr_set = true;
+            }
+            switch (mu) {
+                case 0: k_subsweep_fused<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 1: k_subsweep_fused<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 2: k_subsweep_fused<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                default: k_subsweep_fused<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+            }
+#elif VS_RING_DEPTH == 8
             constexpr int sm = ring8_smem_bytes<NC>();
             static bool attr_set = false;
             if (!attr_set) {
