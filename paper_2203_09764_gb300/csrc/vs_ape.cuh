@@ -158,11 +158,12 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     ape_count(a, reject, singular);
 }
 
-// FP32 over-improved AUS+UCP with the link ring of k_subsweep_ring.
+// FP32 over-improved AUS+UCP with the one-pass link stream of k_subsweep_fused.
 template <int NC, int MU>
 __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeParams a) {
-    __shared__ float4 ring4[kRingDepth * (NC / 4) * VS_RING_THREADS];
-    __shared__ float2 ring2[NC == 18 ? kRingDepth * VS_RING_THREADS : 1];
+    extern __shared__ float4 ape_dyn[];
+    float4 *ring4 = ape_dyn;
+    float2 *ring2 = reinterpret_cast<float2 *>(ape_dyn + 6 * (NC / 4) * VS_RING_THREADS);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
     bool reject = false, singular = false;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeP
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
         const M3<float> Vb =
-            staple_sum_ring<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
+            staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
         ape_finish<float, NC, MU>(a, x, i, Vb, Ux, reject, singular);
     }
     ape_count(a, reject, singular);
@@ -228,11 +229,20 @@ cudaError_t launch_ape_tpl(bool rect, int mu, const ApeParams &p, cudaStream_t s
         // mu from the previous field) the plain-load kernel measured faster
         if (rect && p.colour >= 0) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
+            constexpr int sm = ring6_smem_bytes<NC>();
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_ape_ring<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_ape_ring<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_ape_ring<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_ape_ring<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                attr_set = true;
+            }
             switch (mu) {
-                case 0: k_ape_ring<NC, 0><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                case 1: k_ape_ring<NC, 1><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                case 2: k_ape_ring<NC, 2><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                default: k_ape_ring<NC, 3><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                case 0: k_ape_ring<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 1: k_ape_ring<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 2: k_ape_ring<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                default: k_ape_ring<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
             }
             count_launches(1);
             return cudaGetLastError();

@@ -1277,11 +1277,12 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     }
 }
 
-// FP32 over-improved AUS with the link ring of k_subsweep_ring.
+// FP32 over-improved AUS with the one-pass link stream of k_subsweep_fused.
 template <int NC, int MU>
 __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_aus_ring(AusParams a) {
-    __shared__ float4 ring4[kRingDepth * (NC / 4) * VS_RING_THREADS];
-    __shared__ float2 ring2[NC == 18 ? kRingDepth * VS_RING_THREADS : 1];
+    extern __shared__ float4 aus_dyn[];
+    float4 *ring4 = aus_dyn;
+    float2 *ring2 = reinterpret_cast<float2 *>(aus_dyn + 6 * (NC / 4) * VS_RING_THREADS);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
     bool reject = false;
@@ -1291,7 +1292,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_aus_ring(AusP
         const int i = sidx(g, x);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
-        const M3<float> Vb = staple_sum_ring<NC, MU>(g, static_cast<const float *>(a.U), x, a.c0_f, a.c1_f, R, Ux);
+        const M3<float> Vb = staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.U), x, a.c0_f, a.c1_f, R, Ux);
         aus_finish<float, NC, MU>(a, x, i, Vb, Ux, reject);
     }
     if (a.counters) {

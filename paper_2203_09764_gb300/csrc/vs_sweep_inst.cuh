@@ -89,11 +89,20 @@ cudaError_t launch_aus_tpl(bool rect, int mu, const AusParams &p, cudaStream_t s
         // FP32 over-improved staples: the link-ring kernel
         if (rect) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
+            constexpr int sm = ring6_smem_bytes<NC>();
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_aus_ring<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_aus_ring<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_aus_ring<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_aus_ring<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                attr_set = true;
+            }
             switch (mu) {
-                case 0: k_aus_ring<NC, 0><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                case 1: k_aus_ring<NC, 1><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                case 2: k_aus_ring<NC, 2><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                default: k_aus_ring<NC, 3><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
+                case 0: k_aus_ring<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 1: k_aus_ring<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 2: k_aus_ring<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                default: k_aus_ring<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
             }
             count_launches(1);
             return cudaGetLastError();
