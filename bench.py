@@ -214,6 +214,9 @@ def run_ours(args):
     if not args.no_e2e:
         out_host = torch.empty((4, V, 3, 3), dtype=torch.complex128, pin_memory=True)
         e2e_steps = max(1, min(args.steps, 3))
+        # one untimed pass: the first host read-back sizes the field's staging buffer
+        step(from_host=True)
+        vs.vs_read_field(f, out_host)
         _barrier(dist)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
