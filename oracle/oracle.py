@@ -15,7 +15,7 @@ __all__ = [
     "label_matrix", "labels", "links_from_labels", "splitmix64", "centrifuge_pair",
     "centrifuge", "overimproved_coeffs", "staple_sum", "expm", "stout_generator",
     "colour", "smooth", "action", "centre_charges", "vortex_check", "gauge_transform",
-    "cool", "aus", "maxretr", "observables", "ucp", "ape_ucp", "flow_rk3", "ANNEALED", "SIMULTANEOUS",
+    "cool", "aus", "maxretr", "observables", "reunit", "ucp", "ape_ucp", "flow_rk3", "ANNEALED", "SIMULTANEOUS",
 ]
 
 ANNEALED = 0
@@ -115,6 +115,7 @@ def _declare(L):
         "or_maxretr": (ctypes.c_int, [P, P, ctypes.c_int, P]),
         "or_observables": (ctypes.c_int, [P, P, P, P, P, P]),
         "or_ucp": (ctypes.c_int, [P, P]),
+        "or_reunit": (ctypes.c_int, [ctypes.c_long, P, P]),
         "or_ape_ucp": (ctypes.c_int, [P, P, P, ctypes.c_int, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                       P, ctypes.c_int, P]),
         "or_flow_rk3": (ctypes.c_int, [P, P, ctypes.c_int, dbl, dbl, dbl, ctypes.c_int]),
@@ -326,6 +327,15 @@ def maxretr(U, V, n_hits=3):
     Vc = _c128(V, (3, 3))
     out = np.empty((3, 3), dtype=np.complex128)
     _check(lib().or_maxretr(_p(Uc), _p(Vc), n_hits, _p(out)), "maxretr")
+    return out
+
+
+def reunit(M):
+    """Gram-Schmidt re-unitarisation of a stack of 3x3 matrices (rows 0, 1
+    orthonormalised in order, row 2 = conj(r0 x r1)); any leading shape."""
+    Mc = np.ascontiguousarray(M, dtype=np.complex128)
+    out = np.empty_like(Mc)
+    _check(lib().or_reunit(Mc.size // 9, _p(Mc), _p(out)), "reunit")
     return out
 
 

@@ -923,6 +923,35 @@ static int ucp_project(const mat3 *V, mat3 *out) {
     return 0;
 }
 
+/* Re-unitarisation of n matrices (not a step of the paper: the FP32 storage
+ * modes apply it every few sweeps to undo rounding drift).  Gram-Schmidt on the
+ * rows: r0 <- r0 / |r0|; r1 <- r1 - <r0, r1> r0 with <a, b> = sum conj(a_k) b_k,
+ * r1 <- r1 / |r1|; r2 <- conj(r0 x r1), the row that makes the matrix special
+ * unitary. */
+int or_reunit(long n, const double *in18, double *out18) {
+    if (n < 0) return -1;
+    for (long l = 0; l < n; ++l) {
+        mat3 M;
+        memcpy(&M, in18 + 18 * l, sizeof M);
+        cplx *r0 = M.m[0], *r1 = M.m[1], *r2 = M.m[2];
+        double n0 = 0.0;
+        for (int k = 0; k < 3; ++k) n0 += creal(r0[k] * conj(r0[k]));
+        for (int k = 0; k < 3; ++k) r0[k] /= sqrt(n0);
+        cplx ip = 0.0;
+        for (int k = 0; k < 3; ++k) ip += conj(r0[k]) * r1[k];
+        for (int k = 0; k < 3; ++k) r1[k] -= ip * r0[k];
+        double n1 = 0.0;
+        for (int k = 0; k < 3; ++k) n1 += creal(r1[k] * conj(r1[k]));
+        for (int k = 0; k < 3; ++k) r1[k] /= sqrt(n1);
+        for (int k = 0; k < 3; ++k) {
+            const int a = (k + 1) % 3, b = (k + 2) % 3;
+            r2[k] = conj(r0[a] * r1[b] - r0[b] * r1[a]);
+        }
+        memcpy(out18 + 18 * l, &M, sizeof M);
+    }
+    return 0;
+}
+
 /* One projection of a single matrix (for the pins): 0, or 1 if singular. */
 int or_ucp(const double *V18, double *out18) {
     mat3 V, P;

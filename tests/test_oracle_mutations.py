@@ -99,6 +99,14 @@ MUTATIONS = [
      "sr += 0.5 * creal(m_trace(&FF));",
      "sr += creal(m_trace(&FF));",
      pins.test_reconstructed_action_on_uniform_flux, ()),
+    ("re-unitarisation projects with <r1, r0>",
+     "for (int k = 0; k < 3; ++k) ip += conj(r0[k]) * r1[k];",
+     "for (int k = 0; k < 3; ++k) ip += r0[k] * conj(r1[k]);",
+     pins.test_reunit_rows_are_the_qr_factor_and_special_unitary, ()),
+    ("re-unitarisation third row not conjugated",
+     "r2[k] = conj(r0[a] * r1[b] - r0[b] * r1[a]);",
+     "r2[k] = r0[a] * r1[b] - r0[b] * r1[a];",
+     pins.test_reunit_rows_are_the_qr_factor_and_special_unitary, ()),
     ("cooling subgroup conjugation",
      "Tc.m[p][q] = -be / k;",
      "Tc.m[p][q] = be / k;",

@@ -856,6 +856,36 @@ def test_ucp_closed_forms():
         assert np.abs(P - np.exp(-2j * np.pi * k / 3) * np.eye(3)).max() < 1e-13
 
 
+def test_reunit_rows_are_the_qr_factor_and_special_unitary():
+    """Gram-Schmidt of rows 0, 1 is the QR factorisation of M^T with a positive
+    real diagonal of R (LAPACK through numpy, an independent routine); row 2
+    then makes the matrix special unitary."""
+    rng = np.random.default_rng(75)
+    M = rng.normal(size=(200, 3, 3)) + 1j * rng.normal(size=(200, 3, 3))
+    R = O.reunit(M)
+    for n in range(len(M)):
+        Q, Rr = np.linalg.qr(M[n].T)
+        ph = np.diag(Rr) / np.abs(np.diag(Rr))
+        Q = Q * ph[None, :]
+        assert np.abs(R[n, :2] - Q[:, :2].T).max() < 1e-12
+        assert np.abs(R[n] @ R[n].conj().T - np.eye(3)).max() < 1e-13
+        assert abs(np.linalg.det(R[n]) - 1) < 1e-13
+
+
+def test_reunit_closed_forms():
+    """SU(3) is left alone; a positive multiple of SU(3) returns it; a small
+    perturbation moves by the perturbation's order; r2 of the input is ignored."""
+    Us = _rand_su3(30, 76)
+    assert np.abs(O.reunit(Us) - Us).max() < 1e-14
+    assert np.abs(O.reunit(2.5 * Us) - Us).max() < 1e-14
+    rng = np.random.default_rng(77)
+    D = 1e-6 * (rng.normal(size=Us.shape) + 1j * rng.normal(size=Us.shape))
+    assert np.abs(O.reunit(Us + D) - Us).max() < 1e-5
+    Z = Us.copy()
+    Z[:, 2] = rng.normal(size=(30, 3))
+    assert np.abs(O.reunit(Z) - Us).max() < 1e-14
+
+
 def test_ucp_of_a_singular_matrix_is_undefined():
     assert O.ucp(np.zeros((3, 3))) is None
     V = np.diag([1.0, 2.0, 0.0]).astype(np.complex128)
