@@ -3,7 +3,7 @@
 One step = the whole path on one synthetic 32^3 x 64 field: load the Z(3)
 labels, centrifuge preconditioning (omega = 0.02), 300 annealed over-improved
 stout sweeps (eps = -0.25, rho = 0.06) with the vortex-preservation test and
-FP64 re-unitarisation every 10 sweeps, then the action and the vortex check,
+re-unitarisation every 10 sweeps, then the action and the vortex check,
 in FP32 with 18-real links.  The input labels come from the library's cooled
 hot start (Haar SU(3), 20 MaxReTr cooling sweeps, Z(3) projection; seed 3 +
 rank).  The metric is link updates per second (4 V n_sweeps per step).
@@ -236,7 +236,7 @@ def run_ours(args):
             "config": {"workload": "32^3x64 cooled hot start (Haar SU(3) seed 3+rank, 20 MaxReTr "
                                    "cooling sweeps, Z(3) projection); centrifuge w=0.02; "
                                    "over-improved stout eps=-0.25 rho=0.06 u0=1, %d annealed sweeps "
-                                   "with vortex preservation, FP64 re-unitarisation every 10; "
+                                   "with vortex preservation, re-unitarisation every 10; "
                                    "FP32 18-real links" % args.sweeps,
                        "lattice": list(DIMS), "sweeps": args.sweeps, "precision": "fp32",
                        "storage": "18-real", "parallelism": "replicas" if world > 1 else "1 GPU",

@@ -1,5 +1,6 @@
 // vs_kernels.cu -- load/read conversions, centrifuge, action, vortex check,
 // re-unitarisation, hot-start generation and the exponential diagnostic.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -13,6 +14,8 @@ namespace {
 constexpr int kThreads = 256;
 
 inline int nblocks(long long n, int threads = kThreads) { return (int)((n + threads - 1) / threads); }
+// grid of the grid-stride kernels that first build a per-block table
+constexpr int kTableGrid = 2048;
 
 // ---------------------------------------------------------------------------
 // Load / read
@@ -20,21 +23,33 @@ inline int nblocks(long long n, int threads = kThreads) { return (int)((n + thre
 
 // Z_mu(x) = exp(2 pi i n / 3) I, Sec. I Eq. (centre_project).  One thread per link.
 template <class T, int NC>
-__global__ void k_load_labels(Geo g, const int8_t *__restrict__ lab, T *U, int8_t *ref) {
-    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= 4ll * g.V) return;
-    int mu = (int)(l / g.V), s = (int)(l % g.V);
-    int n = lab[l];
-    Pt p = site_of_lex(g, s);
-    int i = sidx(g, p);
-    double sn, cs;
-    sincospi(2.0 * n / 3.0, &sn, &cs);
-    M3<T> z;
-    m3_zero(z);
-    z.re[0] = z.re[4] = z.re[8] = T(cs);
-    z.im[0] = z.im[4] = z.im[8] = T(sn);
-    store_link<T, NC>(U, g.P, mu, i, z);
-    ref[(long long)mu * g.P + i] = (int8_t)n;
+__global__ void __launch_bounds__(kThreads) k_load_labels(Geo g, const int8_t *__restrict__ lab, T *U, int8_t *ref) {
+    // e^{2 pi i n / 3} for n = -1, 0, 1, three sincospi per block instead of one
+    // per link (the FP64 sincospi made this kernel FP64-bound); labels outside
+    // {-1, 0, 1} (possible only from device input) take the direct evaluation.
+    __shared__ double zc[3], zs[3];
+    if (threadIdx.x < 3) sincospi(2.0 * ((int)threadIdx.x - 1) / 3.0, &zs[threadIdx.x], &zc[threadIdx.x]);
+    __syncthreads();
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < 4ll * g.V;
+         l += (long long)gridDim.x * blockDim.x) {
+        int mu = (int)(l / g.V), s = (int)(l % g.V);
+        int n = lab[l];
+        Pt p = site_of_lex(g, s);
+        int i = sidx(g, p);
+        double sn, cs;
+        if (n >= -1 && n <= 1) {
+            sn = zs[n + 1];
+            cs = zc[n + 1];
+        } else {
+            sincospi(2.0 * n / 3.0, &sn, &cs);
+        }
+        M3<T> z;
+        m3_zero(z);
+        z.re[0] = z.re[4] = z.re[8] = T(cs);
+        z.im[0] = z.im[4] = z.im[8] = T(sn);
+        store_link<T, NC>(U, g.P, mu, i, z);
+        ref[(long long)mu * g.P + i] = (int8_t)n;
+    }
 }
 
 // Links from FP64 host layout; the reference label is the sector of arg Tr U of the FP64 input.
@@ -98,44 +113,70 @@ __global__ void k_current_labels(Geo g, const T *__restrict__ U, int8_t *out) {
 // + n_nu(x-nu+mu)] so that sigma = m 2 pi / 18; delta = omega (sigma - lambda)
 // = omega pi (m - 6n) / 9.  Pair p = SplitMix64(seed, mu V + s) mod 3 picks
 // (j,k) = (0,1), (1,2), (2,0): phase j gets lambda + delta, phase k lambda - delta.
+// The phases take few values: pi (2n/3 + s omega k/9) with n in {-1, 0, 1},
+// k = m - 6n in [-24, 24], s = +-1 (k = 0 is the untouched phase 2n/3).  Each
+// block evaluates them once into shared memory with the same FP64 expressions
+// as the per-link form, so the links are bit-identical to it; values outside
+// the table (labels outside {-1, 0, 1}, only from device input) are evaluated
+// directly.
+constexpr int kCtabK = 24, kCtabN = 3 * (2 * kCtabK + 1) * 2;
+
+__device__ __forceinline__ double centrifuge_phase(double omega, int n, int k, bool neg) {
+    const double delta = omega * (double)k / 9.0;   // in units of pi
+    const double ph = 2.0 * n / 3.0;
+    return neg ? ph - delta : ph + delta;
+}
+
 template <class T, int NC>
-__global__ void k_centrifuge(Geo g, const int8_t *__restrict__ ref, double omega, uint64_t seed, T *U) {
-    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= 4ll * g.V) return;
-    int mu = (int)(l / g.V), s = (int)(l % g.V);
-    Pt x = site_of_lex(g, s);
-    auto lab = [&](int d, const Pt &p) { return (int)ref[(long long)d * g.P + sidx(g, p)]; };
-    int m = 0;
-#pragma unroll
-    for (int j = 1; j < 4; ++j) {
-        int nu = (mu + j) & 3;
-        Pt xpn = mv(g, x, nu, 1), xpm = mv(g, x, mu, 1), xmn = mv(g, x, nu, -1);
-        Pt xmnpm = mv(g, xmn, mu, 1);
-        m += lab(nu, x) + lab(mu, xpn) - lab(nu, xpm) - lab(nu, xmn) + lab(mu, xmn) + lab(nu, xmnpm);
-    }
-    int n = lab(mu, x);
-    double delta = omega * (double)(m - 6 * n) / 9.0;   // in units of pi
-    int pair = (int)(splitmix64(seed, (uint64_t)mu * (uint64_t)g.V + (uint64_t)s) % 3ull);
-    int jj = pair, kk = (pair + 1) % 3;
-    double ph[3];
-    ph[0] = ph[1] = ph[2] = 2.0 * n / 3.0;
-    ph[jj] += delta;
-    ph[kk] -= delta;
-    M3<T> z;
-    m3_zero(z);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
+__global__ void __launch_bounds__(kThreads) k_centrifuge(Geo g, const int8_t *__restrict__ ref, double omega,
+                                                          uint64_t seed, T *U) {
+    __shared__ double2 tab[kCtabN];   // (cos, sin) at ((n + 1)(2K + 1) + k + K) * 2 + neg
+    for (int e = threadIdx.x; e < kCtabN; e += blockDim.x) {
+        const int q = e >> 1;
         double sn, cs;
-        sincospi(ph[k], &sn, &cs);
-        z.re[4 * k] = T(cs);
-        z.im[4 * k] = T(sn);
+        sincospi(centrifuge_phase(omega, q / (2 * kCtabK + 1) - 1, q % (2 * kCtabK + 1) - kCtabK, e & 1), &sn, &cs);
+        tab[e] = make_double2(cs, sn);
     }
-    store_link<T, NC>(U, g.P, mu, sidx(g, x), z);
+    __syncthreads();
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < 4ll * g.V;
+         l += (long long)gridDim.x * blockDim.x) {
+        int mu = (int)(l / g.V), s = (int)(l % g.V);
+        Pt x = site_of_lex(g, s);
+        auto lab = [&](int d, const Pt &p) { return (int)ref[(long long)d * g.P + sidx(g, p)]; };
+        int m = 0;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            int nu = (mu + j) & 3;
+            Pt xpn = mv(g, x, nu, 1), xpm = mv(g, x, mu, 1), xmn = mv(g, x, nu, -1);
+            Pt xmnpm = mv(g, xmn, mu, 1);
+            m += lab(nu, x) + lab(mu, xpn) - lab(nu, xpm) - lab(nu, xmn) + lab(mu, xmn) + lab(nu, xmnpm);
+        }
+        const int n = lab(mu, x), k = m - 6 * n;
+        int pair = (int)(splitmix64(seed, (uint64_t)mu * (uint64_t)g.V + (uint64_t)s) % 3ull);
+        int jj = pair, kk = (pair + 1) % 3;
+        M3<T> z;
+        m3_zero(z);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int kc = c == jj ? k : c == kk ? k : 0;
+            const bool neg = c == kk;
+            double2 v;
+            if (n >= -1 && n <= 1 && kc >= -kCtabK && kc <= kCtabK) {
+                v = tab[((n + 1) * (2 * kCtabK + 1) + kc + kCtabK) * 2 + neg];
+            } else {
+                sincospi(centrifuge_phase(omega, n, kc, neg), &v.y, &v.x);
+            }
+            z.re[4 * c] = T(v.x);
+            z.im[4 * c] = T(v.y);
+        }
+        store_link<T, NC>(U, g.P, mu, sidx(g, x), z);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Wilson action, Sec. V: sum_x sum_{mu<nu} (3 - Re Tr P_munu(x)), FP64 sums
-// in a fixed order (block tree, then one block over the partials).
+// Wilson action, Sec. V: sum_x sum_{mu<nu} (3 - Re Tr P_munu(x)); each
+// plaquette in the storage precision, the sums in FP64 in a fixed order
+// (block tree, then one block over the partials).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -171,11 +212,13 @@ __global__ void __launch_bounds__(kThreads) k_action(Geo g, const T *__restrict_
                 // P = (U_mu(x) U_nu(x+mu)) (U_nu(x) U_mu(x+nu))^dag
                 M3<T> X = m3_mul(Umu, load_link<T, NC>(U, g.P, nu, sidx(g, xm)));
                 M3<T> Y = m3_mul(load_link<T, NC>(U, g.P, nu, i), load_link<T, NC>(U, g.P, mu, sidx(g, xn)));
-                double re = 0;
+                // Re Tr(X Y^dag) in the storage precision: the FP32 products
+                // already carry FP32 rounding, and an FP64 dot (18 conversions
+                // and FMAs on the slow FP64 pipe) made this kernel FP64-bound
+                T re = T(0);
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    re = fma((double)X.re[k], (double)Y.re[k], fma((double)X.im[k], (double)Y.im[k], re));
-                acc += 3.0 - re;
+                for (int k = 0; k < 9; ++k) re = fma(X.re[k], Y.re[k], fma(X.im[k], Y.im[k], re));
+                acc += 3.0 - (double)re;
             }
         }
     }
@@ -359,9 +402,11 @@ __global__ void k_vortex_charges(Geo g, const int8_t *__restrict__ ref, const in
 
 // ---------------------------------------------------------------------------
 // Re-unitarisation: r0 /= |r0|; r1 -= (r0^dag r1) r0; r1 /= |r1|;
-// r2 = conj(r0 x r1).  The norms and the inner product are accumulated in
-// FP64 (the part that decides how unitary the result is); the vector updates
-// run in the storage precision.
+// r2 = conj(r0 x r1), all in the storage precision.  For FP32 links the
+// result is unitary to the rounding of the stored rows (a few 1e-7), the
+// level the FP32 sweeps themselves leave; FP64 norms would buy nothing
+// measurable and make the kernel FP64-bound (GB300's FP64 pipe runs at
+// 1/64 of FP32) instead of HBM-bound.
 // With ref != nullptr (vortex preservation on) a re-unitarised link whose
 // Z(3) label would differ from the reference is left as it was, so every
 // stored link keeps its original label.
@@ -373,32 +418,27 @@ __global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref, const T *_
     if (l >= 4ll * g.V) return;
     int mu = (int)(l / g.V), i = (int)(l % g.V);
     M3<T> m = load_link<T, NC>(U, g.P, mu, i);
-    double n0 = 0;
+    T n0 = T(0);
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
-        n0 = fma((double)m.re[b], (double)m.re[b], fma((double)m.im[b], (double)m.im[b], n0));
-    const T s0 = T(1.0 / sqrt(n0));
+    for (int b = 0; b < 3; ++b) n0 = fma(m.re[b], m.re[b], fma(m.im[b], m.im[b], n0));
+    const T s0 = T(1) / sqrt(n0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) { m.re[b] *= s0; m.im[b] *= s0; }
-    double pr = 0, pi = 0;  // r0^dag r1
+    T pr = T(0), pi = T(0);  // r0^dag r1
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        pr = fma((double)m.re[b], (double)m.re[3 + b], fma((double)m.im[b], (double)m.im[3 + b], pr));
-        pi = fma((double)m.re[b], (double)m.im[3 + b], fma(-(double)m.im[b], (double)m.re[3 + b], pi));
+        pr = fma(m.re[b], m.re[3 + b], fma(m.im[b], m.im[3 + b], pr));
+        pi = fma(m.re[b], m.im[3 + b], fma(-m.im[b], m.re[3 + b], pi));
     }
-    const T tpr = T(pr), tpi = T(pi);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        T r1 = m.re[3 + b] - (tpr * m.re[b] - tpi * m.im[b]);
-        T i1 = m.im[3 + b] - (tpr * m.im[b] + tpi * m.re[b]);
-        m.re[3 + b] = r1;
-        m.im[3 + b] = i1;
+        m.re[3 + b] -= pr * m.re[b] - pi * m.im[b];
+        m.im[3 + b] -= pr * m.im[b] + pi * m.re[b];
     }
-    double n1 = 0;
+    T n1 = T(0);
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
-        n1 = fma((double)m.re[3 + b], (double)m.re[3 + b], fma((double)m.im[3 + b], (double)m.im[3 + b], n1));
-    const T s1 = T(1.0 / sqrt(n1));
+    for (int b = 0; b < 3; ++b) n1 = fma(m.re[3 + b], m.re[3 + b], fma(m.im[3 + b], m.im[3 + b], n1));
+    const T s1 = T(1) / sqrt(n1);
 #pragma unroll
     for (int b = 0; b < 3; ++b) { m.re[3 + b] *= s1; m.im[3 + b] *= s1; }
 #pragma unroll
@@ -568,7 +608,7 @@ long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_load_labels(int prec, int nc, const Geo &g, const int8_t *lab, void *U, int8_t *ref,
                                cudaStream_t st) {
-    int b = nblocks(4ll * g.V);
+    int b = std::min(nblocks(4ll * g.V), kTableGrid);
     if (prec == 0) k_load_labels<double, 18><<<b, kThreads, 0, st>>>(g, lab, (double *)U, ref);
     else if (nc == 18) k_load_labels<float, 18><<<b, kThreads, 0, st>>>(g, lab, (float *)U, ref);
     else k_load_labels<float, 12><<<b, kThreads, 0, st>>>(g, lab, (float *)U, ref);
@@ -612,7 +652,7 @@ cudaError_t launch_current_labels(int prec, int nc, const Geo &g, const void *U,
 
 cudaError_t launch_centrifuge(int prec, int nc, const Geo &g, const int8_t *ref, double omega, uint64_t seed,
                               void *U, cudaStream_t st) {
-    int b = nblocks(4ll * g.V);
+    int b = std::min(nblocks(4ll * g.V), kTableGrid);
     if (prec == 0) k_centrifuge<double, 18><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (double *)U);
     else if (nc == 18) k_centrifuge<float, 18><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (float *)U);
     else k_centrifuge<float, 12><<<b, kThreads, 0, st>>>(g, ref, omega, seed, (float *)U);

@@ -60,6 +60,28 @@ def test_exponential_matches_taylor_and_eigendecomposition(ctx, prec, tol):
     assert np.array_equal(vs.vs_debug_expm(ctx, np.zeros((1, 3, 3)), p)[0], np.eye(3))
 
 
+@pytest.mark.parametrize("prec,storage,tol", [("fp64", "link18", 1e-14), ("fp32", "link18", 1e-6),
+                                               ("fp32", "link12", 1e-6)])
+def test_reunitarise_matches_oracle(ctx, prec, storage, tol):
+    """Re-unitarisation of a Haar field with 1e-3 non-unitary noise on every
+    entry, against the oracle's Gram-Schmidt; the FP32 result is unitary to
+    the rounding of its stored rows.  12-real storage keeps rows 0-1 only, so
+    its input row 2 is replaced on load, as the oracle ignores it."""
+    dims = (4, 8, 12, 16)
+    U = synth.haar_field(dims, 80)
+    rng = np.random.default_rng(81)
+    U = U + 1e-3 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64 if prec == "fp64" else vs.VS_FP32,
+                           vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12)
+    vs.vs_load_field(f, links=U)
+    vs.vs_reunitarise(f)
+    Ug = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    assert max_abs(Ug, O.reunit(U)) < tol
+    dev = np.abs(np.einsum("...ij,...kj->...ik", Ug, Ug.conj()) - np.eye(3)).max()
+    assert dev < (1e-14 if prec == "fp64" else 1e-6)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_load_and_centrifuge_match_oracle(ctx, prec):
     p = vs.VS_FP64 if prec == "fp64" else vs.VS_FP32
@@ -87,6 +109,22 @@ def test_load_links_and_labels_from_fp64_input(ctx):
     assert np.array_equal(vs.vs_read_field(f), U)
     assert np.array_equal(vs.vs_read_labels(f), O.labels(dims, U))
     vs.vs_field_destroy(f)
+
+
+@pytest.mark.parametrize("storage", ["link18", "link12"])
+def test_fp32_action_within_rounding(ctx, storage):
+    """FP32 action (plaquette products and traces in FP32, the sum over
+    plaquettes in FP64) of a Haar field and of a centrifuged vortex field,
+    against the oracle's FP64 action of the same links: within 1e-6 absolute
+    (a few FP32 roundings per plaquette, ~1e-7 each)."""
+    dims = (8, 4, 4, 8)
+    st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
+    for U in (synth.haar_field(dims, 4), O.centrifuge(dims, synth.iid_labels(dims, 6), 0.02, 1234)):
+        f = vs.vs_field_create(ctx, dims, vs.VS_FP32, st)
+        vs.vs_load_field(f, links=U)
+        S = vs.vs_action(f)
+        vs.vs_field_destroy(f)
+        assert abs(S - O.action(dims, U)) < 1e-6
 
 
 def test_action_and_vortex_check_match_oracle(ctx):
