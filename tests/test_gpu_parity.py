@@ -263,6 +263,50 @@ def test_fp32_each_sweep_within_fp32_rounding_of_fp64(ctx, storage, vp):
     assert ties <= 8
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (4, 4, 12, 20)])
+@pytest.mark.parametrize("storage", ["link18", "link12"])
+def test_fp32_class_kernel_general_su3_ragged(ctx, dims, storage):
+    """The FP32 class kernel (the benchmark's path) on a general SU(3) field,
+    so that every entry of the two-row chains and rebuilt rows matters, at
+    lattices whose class launches end in a partial block: 4^4 (64 threads of a
+    128-thread block, and +-2 shifts land on the same site) and 4x4x12x20
+    (960 threads, 7.5 blocks).  Each sweep starts both sides from the oracle's
+    FP64 field; FP32 within 1e-6."""
+    U = O.cool(dims, synth.haar_field(dims, 31), 2)
+    st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, st)
+    worst = 0.0
+    for sweep in range(3):
+        vs.vs_load_field(f, links=U)
+        vs.vs_smooth(f, 1, 0.06, -0.25, vortex_preserve=False, reunit_every=0)
+        Ug = vs.vs_read_field(f)
+        U, _ = O.smooth(dims, U, None, 1, 0.06, eps=-0.25, vp=False)
+        worst = max(worst, max_abs(Ug, U))
+    vs.vs_field_destroy(f)
+    assert worst < 1e-6
+
+
+def test_zero_sweeps_and_bad_extents(ctx):
+    """n_sweeps = 0 leaves the field bit for bit; extents that are not positive
+    multiples of 4 (the annealing schedule's requirement) or a lattice above
+    2^30 sites are rejected with VS_EINVAL before any allocation."""
+    dims = (4, 8, 4, 4)
+    U = O.cool(dims, synth.haar_field(dims, 32), 1)
+    for prec in (vs.VS_FP64, vs.VS_FP32):
+        f = vs.vs_field_create(ctx, dims, prec, vs.VS_LINK18)
+        vs.vs_load_field(f, links=U)
+        U0 = vs.vs_read_field(f)
+        assert vs.vs_smooth(f, 0, 0.06, -0.25, stats=True) == []
+        vs.vs_smooth_aus(f, 0, 0.02, -0.25)
+        vs.vs_flow_rk3(f, 0, 0.02)
+        assert np.array_equal(vs.vs_read_field(f), U0)
+        vs.vs_field_destroy(f)
+    for bad in [(0, 4, 4, 4), (6, 4, 4, 4), (4, 4, 4, -4), (4, 4, 2, 4), (2048, 2048, 2048, 4)]:
+        with pytest.raises(vs.VSError) as ei:
+            vs.vs_field_create(ctx, bad, vs.VS_FP32, vs.VS_LINK18)
+        assert ei.value.status == vs.VS_EINVAL
+
+
 def test_fp32_vp_200_free_running_sweeps_keep_vortex_structure(ctx):
     """200 free-running FP32 sweeps with VP: every label and centre charge
     equals the original (and the FP64 oracle's), and the mean action, a
