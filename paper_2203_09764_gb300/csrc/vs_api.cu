@@ -776,6 +776,11 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
     p.h_f = (float)p.h;
     p.c0_f = (float)p.c0;
     p.c1_f = (float)p.c1;
+    // Every link of a stage is computed from the previous stage's field, so the
+    // field and the scratch buffer alternate as source and destination (every
+    // link of the destination is written); one copy at the end if the last
+    // stage wrote the scratch buffer.
+    void *cur = f->U, *nxt = f->scratch;
     for (int s = 0; s < n_steps; ++s) {
         p.counters = stats ? f->sweep_counts + 2 * s : nullptr;
         for (int k = 0; k < 3; ++k) {
@@ -785,12 +790,15 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
             p.a_f = (float)p.a;
             p.b_f = (float)p.b;
             p.c_f = (float)p.c;
-            CK(cudaMemcpyAsync(f->scratch, f->U, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
+            p.Usrc = cur;
+            p.U = nxt;
             for (int mu = 0; mu < 4; ++mu) CK(flow_launch(f, rect, mu, p));
+            std::swap(cur, nxt);
         }
         if (f->prec == VS_FP32 && reunit_every > 0 && (f->sweeps_done + s + 1) % reunit_every == 0)
-            CK(launch_reunit(1, f->nc, f->g, f->U, nullptr, f->stream, nullptr));
+            CK(launch_reunit(1, f->nc, f->g, cur, nullptr, f->stream, nullptr));
     }
+    if (cur != f->U) CK(cudaMemcpyAsync(f->U, cur, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
     f->sweeps_done += n_steps;
     if (!stats) return VS_OK;
     std::vector<unsigned long long> cnt(2 * (size_t)n_steps);

@@ -142,6 +142,28 @@ def test_flow_rk3_fp32_each_step_within_rounding(ctx, storage):
     assert worst < 2e-6
 
 
+@pytest.mark.parametrize("n_steps", [2, 3])
+def test_flow_rk3_reunitarises_the_live_field(ctx, n_steps):
+    """The stages alternate between the field and a scratch buffer (6 stages
+    end in the field, 9 in the scratch buffer); re-unitarisation after the last
+    step must act on the buffer that holds the current links.  Input links
+    carry 1e-3 of non-unitary noise, which the flow keeps and only the
+    re-unitarisation removes."""
+    dims = (8, 4, 4, 8)
+    U = O.cool(dims, synth.haar_field(dims, 53), 2)
+    rng = np.random.default_rng(54)
+    U = U + 1e-3 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    devs = []
+    for every in (0, n_steps):
+        vs.vs_load_field(f, links=U)
+        vs.vs_flow_rk3(f, n_steps, 0.02, -0.25, reunit_every=every)
+        Ug = vs.vs_read_field(f)
+        devs.append(np.abs(np.einsum("...ij,...kj->...ik", Ug, Ug.conj()) - np.eye(3)).max())
+    vs.vs_field_destroy(f)
+    assert devs[0] > 1e-4 and devs[1] < 1e-6
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_flow_rk3_leaves_a_vortex_field_unchanged(ctx, precision):
     """Q = 0 exactly on a centre-vortex field (Sec. V.B): bitwise unchanged."""
