@@ -180,45 +180,84 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeP
     ape_count(a, reject, singular);
 }
 
-// One Runge-Kutta stage for every link of direction MU (thread t = plane
-// position t): H_Z = -i h Q[W_i], H_S <- a H_Z + b H_S, W_{i+1} = exp(i c H_S) W_i.
-template <class T, int NC, bool RECT, int MU>
-__global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1)
-    k_flow_stage(FlowParams a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = t < a.n_threads;
-    bool used64 = false;
-    if (active) {
-        const Geo &g = a.g;
-        const Pt x = site_of_index(g, t);
-        const int i = t;
-        const T *Us = static_cast<const T *>(a.Usrc);
-        const bool f32 = sizeof(T) == 4;
-        const T c0 = f32 ? T(a.c0_f) : T(a.c0), c1 = f32 ? T(a.c1_f) : T(a.c1);
-        const T h = f32 ? T(a.h_f) : T(a.h), ca = f32 ? T(a.a_f) : T(a.a);
-        const T cb = f32 ? T(a.b_f) : T(a.b), cc = f32 ? T(a.c_f) : T(a.c);
-        const M3<T> sig = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
-        const M3<T> u = load_link<T, NC>(Us, g.P, MU, i);
-        T hz[9];
-        stout_H<T>(sig, u, h, hz);
-        T *S = static_cast<T *>(a.S) + (long long)MU * 9 * g.P;
-        T hs[9];
+// End of one Runge-Kutta stage for link (MU, i) from its staple sum sig and
+// link u: H_Z = -i h Q[W_i], H_S <- a H_Z + b H_S, W_{i+1} = exp(i c H_S) W_i.
+template <class T, int NC, int MU>
+__device__ __forceinline__ void flow_finish(const FlowParams &a, int i, const M3<T> &sig, const M3<T> &u,
+                                            bool &used64) {
+    const Geo &g = a.g;
+    const bool f32 = sizeof(T) == 4;
+    const T h = f32 ? T(a.h_f) : T(a.h), ca = f32 ? T(a.a_f) : T(a.a);
+    const T cb = f32 ? T(a.b_f) : T(a.b), cc = f32 ? T(a.c_f) : T(a.c);
+    T hz[9];
+    stout_H<T>(sig, u, h, hz);
+    T *S = static_cast<T *>(a.S) + (long long)MU * 9 * g.P;
+    T hs[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            hs[k] = ca * hz[k];
-            if (cb != T(0)) hs[k] = fma(cb, S[(long long)k * g.P + i], hs[k]);
-            S[(long long)k * g.P + i] = hs[k];
-        }
-        const M3<T> E = exp_iH<T>(cc * hs[0], cc * hs[1], cc * hs[2], cc * hs[3], cc * hs[4], cc * hs[5],
-                                  cc * hs[6], cc * hs[7], cc * hs[8], used64);
-        M3<T> un = m3_mul(E, u);
-        if (NC == 12) rebuild_row2(un);
-        store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, un);
+    for (int k = 0; k < 9; ++k) {
+        hs[k] = ca * hz[k];
+        if (cb != T(0)) hs[k] = fma(cb, S[(long long)k * g.P + i], hs[k]);
+        S[(long long)k * g.P + i] = hs[k];
     }
+    const M3<T> E = exp_iH<T>(cc * hs[0], cc * hs[1], cc * hs[2], cc * hs[3], cc * hs[4], cc * hs[5],
+                              cc * hs[6], cc * hs[7], cc * hs[8], used64);
+    M3<T> un = m3_mul(E, u);
+    if (NC == 12) rebuild_row2(un);
+    store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, un);
+}
+
+__device__ __forceinline__ void flow_count(const FlowParams &a, bool used64) {
     if (a.counters) {
         const unsigned fb = __ballot_sync(0xffffffffu, used64);
         if ((threadIdx.x & 31) == 0 && fb) atomicAdd(&a.counters[1], (unsigned long long)__popc(fb));
     }
+}
+
+// One Runge-Kutta stage for every link of direction MU (thread t = plane
+// position t), staples from plain loads (FP64, and FP32 without the ring).
+template <class T, int NC, bool RECT, int MU>
+__global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1)
+    k_flow_stage(FlowParams a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool used64 = false;
+    if (t < a.n_threads) {
+        const Geo &g = a.g;
+        const Pt x = site_of_index(g, t);
+        const T *Us = static_cast<const T *>(a.Usrc);
+        const bool f32 = sizeof(T) == 4;
+        const T c0 = f32 ? T(a.c0_f) : T(a.c0), c1 = f32 ? T(a.c1_f) : T(a.c1);
+        const M3<T> sig = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
+        const M3<T> u = load_link<T, NC>(Us, g.P, MU, t);
+        flow_finish<T, NC, MU>(a, t, sig, u, used64);
+    }
+    flow_count(a, used64);
+}
+
+// The same stage in FP32 with the staple links streamed through the per-thread
+// cp.async ring: the one-pass stream of the class kernel for over-improved
+// staples, the plaquette-staple ring for eps = 1.
+template <int NC, bool RECT, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, RECT ? VS_RING_MINB : 4) k_flow_stage_ring(FlowParams a) {
+    extern __shared__ float4 flow_dyn[];
+    float4 *ring4 = flow_dyn;
+    float2 *ring2 = reinterpret_cast<float2 *>(flow_dyn + 6 * (NC / 4) * VS_RING_THREADS);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool used64 = false;
+    if (t < a.n_threads) {
+        const Geo &g = a.g;
+        const Pt x = site_of_index(g, t);
+        const float *Us = static_cast<const float *>(a.Usrc);
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
+        M3<float> sig, u;
+        if constexpr (RECT) {
+            sig = staple_sum_fused<NC, MU>(g, Us, x, a.c0_f, a.c1_f, R, u);
+        } else {
+            sig = staple_sum_plain_ring<NC, MU>(g, Us, x, a.c0_f, R);
+            u = load_link<float, NC>(Us, g.P, MU, t);
+        }
+        flow_finish<float, NC, MU>(a, t, sig, u, used64);
+    }
+    flow_count(a, used64);
 }
 
 template <class T, int NC>
@@ -273,9 +312,44 @@ cudaError_t launch_ape_tpl(bool rect, int mu, const ApeParams &p, cudaStream_t s
 
 template <class T, int NC>
 cudaError_t launch_flow_tpl(bool rect, int mu, const FlowParams &p, cudaStream_t st) {
+    if (p.n_threads <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4 && VS_RING) {
+        const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
+        constexpr int sm = ring6_smem_bytes<NC>();
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_flow_stage_ring<NC, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            attr_set = true;
+        }
+#define VS_LAUNCH(R, M) k_flow_stage_ring<NC, R, M><<<rb, VS_RING_THREADS, sm, st>>>(p)
+        if (rect) {
+            switch (mu) {
+                case 0: VS_LAUNCH(true, 0); break;
+                case 1: VS_LAUNCH(true, 1); break;
+                case 2: VS_LAUNCH(true, 2); break;
+                default: VS_LAUNCH(true, 3); break;
+            }
+        } else {
+            switch (mu) {
+                case 0: VS_LAUNCH(false, 0); break;
+                case 1: VS_LAUNCH(false, 1); break;
+                case 2: VS_LAUNCH(false, 2); break;
+                default: VS_LAUNCH(false, 3); break;
+            }
+        }
+#undef VS_LAUNCH
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const int threads = VS_SUBSWEEP_THREADS;
     const int blocks = (p.n_threads + threads - 1) / threads;
-    if (blocks == 0) return cudaSuccess;
 #define VS_LAUNCH(R, M) k_flow_stage<T, NC, R, M><<<blocks, threads, 0, st>>>(p)
     if (rect) {
         switch (mu) {

@@ -1098,6 +1098,83 @@ __device__ __forceinline__ M3<float> staple_sum_fused(const Geo &g, const float 
     return sig;
 }
 
+// ---------------------------------------------------------------------------
+// Plaquette staples alone (eps = 1) through the link ring.  A unit (nu, s) is
+// the staple A B C with A = step(x, s nu), B = U_mu(x + s nu), C = step(x +
+// s nu + mu, -s nu) (entries 0, 1 and 9 of a unit of the one-pass stream);
+// units run (nu1, +), (nu1, -), (nu2, +), ...  Six slots hold two units, unit
+// (nu, s) in slots 3 [s = -1] + 0..2, and each slot is refilled with the same
+// entry of (next nu, s).  Every staple is SU(3), so it is formed in rows 0-1
+// and its row 2 rebuilt.
+// ---------------------------------------------------------------------------
+template <int J>
+__host__ __device__ constexpr int p_entry() { return J == 0 ? 0 : (J == 1 ? 1 : 9); }
+
+template <int NC, int S, int J>
+__device__ __forceinline__ void p_refill(const LinkRing<NC> &R, const float *Umu, const float *Un, long long P,
+                                         const Around &An, bool last) {
+    const float *base;
+    int pos;
+    u_link<S, p_entry<J>()>(An, Umu, Un, base, pos);
+    ring_fetch_if<NC, (S < 0 ? 3 : 0) + J>(R, base, P, pos, !last);
+}
+
+template <int NC, int S>
+__device__ __forceinline__ void plain_unit(const LinkRing<NC> &R, M3<float> &sig, const float *Umu,
+                                           const float *Un, long long P, const Around &An, bool last) {
+    constexpr int S0 = S < 0 ? 3 : 0;
+    const M3<float> Af = ring_take6<NC, (S < 0), S0, false>(R);
+    p_refill<NC, S, 0>(R, Umu, Un, P, An, last);
+    const M3<float> B = ring_take6<NC, false, S0 + 1>(R);
+    p_refill<NC, S, 1>(R, Umu, Un, P, An, last);
+    M3<float> X, Y;
+    m3_mul_2r(X, Af, B);
+    const M3<float> C = ring_take6<NC, (S > 0), S0 + 2>(R);
+    p_refill<NC, S, 2>(R, Umu, Un, P, An, last);
+    m3_mul_2r(Y, X, C);
+    rebuild_row2(Y);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { sig.re[k] += Y.re[k]; sig.im[k] += Y.im[k]; }
+}
+
+template <int NC, int MU>
+__device__ __forceinline__ M3<float> staple_sum_plain_ring(const Geo &g, const float *__restrict__ U, Pt x,
+                                                           float c0, const LinkRing<NC> &R) {
+    const long long P = g.P;
+    Around A, An;
+    A.i0 = sidx(g, x);
+    A.dmm1 = 0;
+    A.dmp1 = shift_delta(g, x, MU, 1);
+    A.dmp2 = 0;
+    around_nu(g, x, (MU + 1) & 3, false, A);
+    An = A;
+    const float *Umu = U + (long long)MU * NC * P;
+    const float *Unu = U + (long long)((MU + 1) & 3) * NC * P;
+    {   // prologue: the two units of the first nu
+        const float *b;
+        int q;
+        u_link<1, 0>(A, Umu, Unu, b, q); ring_fetch<NC, 0>(R, b, P, q);
+        u_link<1, 1>(A, Umu, Unu, b, q); ring_fetch<NC, 1>(R, b, P, q);
+        u_link<1, 9>(A, Umu, Unu, b, q); ring_fetch<NC, 2>(R, b, P, q);
+        u_link<-1, 0>(A, Umu, Unu, b, q); ring_fetch<NC, 3>(R, b, P, q);
+        u_link<-1, 1>(A, Umu, Unu, b, q); ring_fetch<NC, 4>(R, b, P, q);
+        u_link<-1, 9>(A, Umu, Unu, b, q); ring_fetch<NC, 5>(R, b, P, q);
+    }
+    M3<float> sig;
+    m3_zero(sig);
+#pragma unroll 1
+    for (int j = 1; j < 4; ++j) {
+        const bool last = j == 3;
+        const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
+        around_nu(g, x, nun, false, An);
+        const float *Un = U + (long long)nun * NC * P;
+        plain_unit<NC, 1>(R, sig, Umu, Un, P, An, last);
+        plain_unit<NC, -1>(R, sig, Umu, Un, P, An, last);
+    }
+    if (c0 != 1.0f) m3_scale(sig, c0);
+    return sig;
+}
+
 template <int NC>
 constexpr int ring6_smem_bytes() {
     return 6 * VS_RING_THREADS * ((NC / 4) * 16 + (NC == 18 ? 8 : 0));
@@ -1112,6 +1189,28 @@ __device__ __forceinline__ LinkRing<NC> ring_of(float4 *ring4, float2 *ring2) {
     R.a4 = (uint32_t)__cvta_generic_to_shared(ring4 + threadIdx.x);
     R.a2 = (uint32_t)__cvta_generic_to_shared(ring2 + (NC == 18 ? threadIdx.x : 0));
     return R;
+}
+
+// FP32 standard-staple class update through the plain link ring.
+template <int NC, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, 4) k_subsweep_pring(SubsweepParams a) {
+    extern __shared__ float4 pring_dyn[];
+    float4 *ring4 = pring_dyn;
+    float2 *ring2 = reinterpret_cast<float2 *>(pring_dyn + 6 * (NC / 4) * VS_RING_THREADS);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false, used64 = false;
+    if (active) {
+        const Geo &g = a.g;
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        const int i = sidx(g, x);
+        const float *Us = static_cast<const float *>(a.Usrc);
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
+        const M3<float> sig = staple_sum_plain_ring<NC, MU>(g, Us, x, a.c0_f, R);
+        const M3<float> Ux = load_link<float, NC>(Us, g.P, MU, i);
+        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
+    }
+    count_update(a, reject, used64);
 }
 
 template <int NC, int MU>

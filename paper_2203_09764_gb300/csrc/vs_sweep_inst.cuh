@@ -12,7 +12,7 @@ template <class T, int NC>
 cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cudaStream_t st) {
     if (p.n_threads <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4 && VS_RING) {
-        // FP32 over-improved staples: the cp.async link-ring kernel
+        // FP32: the cp.async link-ring kernels
         if (rect) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
 #if VS_FUSED
@@ -55,6 +55,26 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
                 default: k_subsweep_ring<NC, 3><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
             }
 #endif
+            count_launches(1);
+            return cudaGetLastError();
+        }
+        {   // FP32 plaquette staples (eps = 1): the plaquette-staple link ring
+            const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
+            constexpr int sm = ring6_smem_bytes<NC>();
+            static bool attr_set_p = false;
+            if (!attr_set_p) {
+                cudaFuncSetAttribute(k_subsweep_pring<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_subsweep_pring<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_subsweep_pring<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_subsweep_pring<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                attr_set_p = true;
+            }
+            switch (mu) {
+                case 0: k_subsweep_pring<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 1: k_subsweep_pring<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 2: k_subsweep_pring<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                default: k_subsweep_pring<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+            }
             count_launches(1);
             return cudaGetLastError();
         }

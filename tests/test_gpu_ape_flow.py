@@ -125,18 +125,26 @@ def test_flow_rk3_fp64_matches_oracle(ctx, eps):
         assert len(st) == 3
 
 
+@pytest.mark.parametrize("eps", [-0.25, 1.0])
 @pytest.mark.parametrize("storage", ["link18", "link12"])
-def test_flow_rk3_fp32_each_step_within_rounding(ctx, storage):
-    dims = (8, 8, 8, 8)
+def test_flow_rk3_fp32_each_step_within_rounding(ctx, storage, eps):
+    """FP32 Runge-Kutta steps (the over-improved and the Wilson flow, whose
+    staples take different link streams) from the oracle's FP64 field, one
+    step at a time; also a lattice whose launches end in a partial block."""
+    for dims in [(8, 8, 8, 8), (4, 4, 12, 20)]:
+        _flow_fp32_steps(ctx, dims, storage, eps)
+
+
+def _flow_fp32_steps(ctx, dims, storage, eps):
     U = O.cool(dims, synth.haar_field(dims, 50), 2)
     st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
     f = vs.vs_field_create(ctx, dims, vs.VS_FP32, st)
     worst = 0.0
     for _ in range(5):
         vs.vs_load_field(f, links=U)
-        vs.vs_flow_rk3(f, 1, 0.05, -0.25, reunit_every=0)
+        vs.vs_flow_rk3(f, 1, 0.05, eps, reunit_every=0)
         Ug = vs.vs_read_field(f)
-        U = O.flow_rk3(dims, U, 1, 0.05, eps=-0.25)
+        U = O.flow_rk3(dims, U, 1, 0.05, eps=eps)
         worst = max(worst, max_abs(Ug, U))
     vs.vs_field_destroy(f)
     assert worst < 2e-6

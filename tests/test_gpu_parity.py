@@ -263,11 +263,13 @@ def test_fp32_each_sweep_within_fp32_rounding_of_fp64(ctx, storage, vp):
     assert ties <= 8
 
 
+@pytest.mark.parametrize("eps", [-0.25, 1.0])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (4, 4, 12, 20)])
 @pytest.mark.parametrize("storage", ["link18", "link12"])
-def test_fp32_class_kernel_general_su3_ragged(ctx, dims, storage):
-    """The FP32 class kernel (the benchmark's path) on a general SU(3) field,
-    so that every entry of the two-row chains and rebuilt rows matters, at
+def test_fp32_class_kernel_general_su3_ragged(ctx, dims, storage, eps):
+    """The FP32 class kernels (over-improved: the benchmark's path; eps = 1:
+    plaquette staples) on a general SU(3) field, so that every entry of the
+    two-row chains and rebuilt rows matters, at
     lattices whose class launches end in a partial block: 4^4 (64 threads of a
     128-thread block, and +-2 shifts land on the same site) and 4x4x12x20
     (960 threads, 7.5 blocks).  Each sweep starts both sides from the oracle's
@@ -278,9 +280,9 @@ def test_fp32_class_kernel_general_su3_ragged(ctx, dims, storage):
     worst = 0.0
     for sweep in range(3):
         vs.vs_load_field(f, links=U)
-        vs.vs_smooth(f, 1, 0.06, -0.25, vortex_preserve=False, reunit_every=0)
+        vs.vs_smooth(f, 1, 0.06, eps, vortex_preserve=False, reunit_every=0)
         Ug = vs.vs_read_field(f)
-        U, _ = O.smooth(dims, U, None, 1, 0.06, eps=-0.25, vp=False)
+        U, _ = O.smooth(dims, U, None, 1, 0.06, eps=eps, vp=False)
         worst = max(worst, max_abs(Ug, U))
     vs.vs_field_destroy(f)
     assert worst < 1e-6
