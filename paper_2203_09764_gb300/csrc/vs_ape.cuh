@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeP
 // link u: H_Z = -i h Q[W_i], H_S <- a H_Z + b H_S, W_{i+1} = exp(i c H_S) W_i.
 template <class T, int NC, int MU>
 __device__ __forceinline__ void flow_finish(const FlowParams &a, int i, const M3<T> &sig, const M3<T> &u,
-                                            bool &used64) {
+                                            bool &used64, const T *s_old = nullptr) {
     const Geo &g = a.g;
     const bool f32 = sizeof(T) == 4;
     const T h = f32 ? T(a.h_f) : T(a.h), ca = f32 ? T(a.a_f) : T(a.a);
@@ -196,7 +196,7 @@ __device__ __forceinline__ void flow_finish(const FlowParams &a, int i, const M3
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         hs[k] = ca * hz[k];
-        if (cb != T(0)) hs[k] = fma(cb, S[(long long)k * g.P + i], hs[k]);
+        if (cb != T(0)) hs[k] = fma(cb, s_old ? s_old[k] : S[(long long)k * g.P + i], hs[k]);
         S[(long long)k * g.P + i] = hs[k];
     }
     const M3<T> E = exp_iH<T>(cc * hs[0], cc * hs[1], cc * hs[2], cc * hs[3], cc * hs[4], cc * hs[5],
@@ -249,13 +249,19 @@ __global__ void __launch_bounds__(VS_RING_THREADS, RECT ? VS_RING_MINB : 4) k_fl
         const float *Us = static_cast<const float *>(a.Usrc);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> sig, u;
+        // the exponent H_S of this link, read before the staple stream so that
+        // its latency hides behind it (stage 1 of a step does not read it)
+        float s_old[9];
+        const float *Sp = static_cast<const float *>(a.S) + (long long)MU * 9 * g.P + t;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s_old[k] = a.b_f != 0.0f ? __ldg(Sp + (long long)k * g.P) : 0.0f;
         if constexpr (RECT) {
             sig = staple_sum_fused<NC, MU>(g, Us, x, a.c0_f, a.c1_f, R, u);
         } else {
             sig = staple_sum_plain_ring<NC, MU>(g, Us, x, a.c0_f, R);
             u = load_link<float, NC>(Us, g.P, MU, t);
         }
-        flow_finish<float, NC, MU>(a, t, sig, u, used64);
+        flow_finish<float, NC, MU>(a, t, sig, u, used64, s_old);
     }
     flow_count(a, used64);
 }
