@@ -124,6 +124,7 @@ __device__ __forceinline__ void ape_finish(const ApeParams &a, const Pt &x, int 
         reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
     }
     if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, un);
+    else if (a.U != a.Usrc) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, u);
 }
 
 __device__ __forceinline__ void ape_count(const ApeParams &a, bool reject, bool singular) {
@@ -270,9 +271,7 @@ template <class T, int NC>
 cudaError_t launch_ape_tpl(bool rect, int mu, const ApeParams &p, cudaStream_t st) {
     if (p.n_threads <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4 && VS_RING) {
-        // annealed classes only: for the simultaneous schedule (every link of
-        // mu from the previous field) the plain-load kernel measured faster
-        if (rect && p.colour >= 0) {
+        if (rect) {   // annealed classes and simultaneous sweeps alike
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
             constexpr int sm = ring6_smem_bytes<NC>();
             static bool attr_set = false;

@@ -513,6 +513,11 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
             f->events.push_back(e);
         }
     }
+    // Simultaneous schedule: every link from the previous field, so the field
+    // and the scratch buffer alternate as source and destination (rejected
+    // links are written with their old value); one copy at the end if the
+    // last sweep wrote the scratch buffer.
+    void *cur = f->U, *nxt = f->scratch;
     for (int s = 0; s < n_sweeps; ++s) {
         const double r = a.rho_per_sweep ? a.rho_per_sweep[s] : rho;
         SubsweepParams p = make_params(f, r, eps, u0, vp);
@@ -526,19 +531,21 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
                     CK(subsweep_launch(f, rect, mu, p));
                 }
         } else {
-            CK(cudaMemcpyAsync(f->scratch, f->U, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
-            p.Usrc = f->scratch;
+            p.Usrc = cur;
+            p.U = nxt;
             p.colour = -1;
             p.n_threads = f->g.V;
             for (int mu = 0; mu < 4; ++mu) CK(subsweep_launch(f, rect, mu, p));
+            std::swap(cur, nxt);
         }
         if (f->profiling) CK(cudaEventRecord(f->events[2 * s + 1], f->stream));
         if (f->prec == VS_FP32 && a.reunit_every > 0 && (f->sweeps_done + s + 1) % a.reunit_every == 0)
-            CK(launch_reunit(1, f->nc, f->g, f->U, vp ? f->ref : nullptr, f->stream,
+            CK(launch_reunit(1, f->nc, f->g, cur, vp ? f->ref : nullptr, f->stream,
                              f->gauge_on ? f->G : nullptr));
         if (want_stats && a.action_every > 0 && (s + 1) % a.action_every == 0)
-            CK(launch_action(f->prec == VS_FP32, f->nc, f->g, f->U, f->partials, f->sweep_actions + s, f->stream));
+            CK(launch_action(f->prec == VS_FP32, f->nc, f->g, cur, f->partials, f->sweep_actions + s, f->stream));
     }
+    if (cur != f->U) CK(cudaMemcpyAsync(f->U, cur, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
     if (f->profiling && n_sweeps > 0) {
         CK(cudaEventSynchronize(f->events[2 * n_sweeps - 1]));
         for (int s = 0; s < n_sweeps; ++s) {
@@ -698,9 +705,11 @@ extern "C" vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, 
     a.c0_f = (float)a.c0;
     a.c1_f = (float)a.c1;
     a.vp = vortex_preserve ? 1 : 0;
+    void *cur = f->U, *nxt = f->scratch;   // simultaneous: alternating buffers, as in vs_smooth
     for (int s = 0; s < n_sweeps; ++s) {
         a.counters = stats ? f->sweep_counts + 2 * s : nullptr;
         if (schedule == VS_ANNEALED) {
+            a.U = f->U;
             a.Usrc = f->U;
             a.n_threads = f->g.V / 4;
             for (int mu = 0; mu < 4; ++mu)
@@ -709,16 +718,18 @@ extern "C" vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, 
                     CK(ape_launch(f, rect, mu, a));
                 }
         } else {
-            CK(cudaMemcpyAsync(f->scratch, f->U, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
-            a.Usrc = f->scratch;
+            a.Usrc = cur;
+            a.U = nxt;
             a.colour = -1;
             a.n_threads = f->g.V;
             for (int mu = 0; mu < 4; ++mu) CK(ape_launch(f, rect, mu, a));
+            std::swap(cur, nxt);
         }
         if (f->prec == VS_FP32 && reunit_every > 0 && (f->sweeps_done + s + 1) % reunit_every == 0)
-            CK(launch_reunit(1, f->nc, f->g, f->U, vortex_preserve ? f->ref : nullptr, f->stream,
+            CK(launch_reunit(1, f->nc, f->g, cur, vortex_preserve ? f->ref : nullptr, f->stream,
                              f->gauge_on ? f->G : nullptr));
     }
+    if (cur != f->U) CK(cudaMemcpyAsync(f->U, cur, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
     f->sweeps_done += n_sweeps;
     if (!stats) return VS_OK;
     std::vector<unsigned long long> cnt(2 * (size_t)n_sweeps);

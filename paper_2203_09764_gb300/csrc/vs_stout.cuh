@@ -334,7 +334,10 @@ __device__ __forceinline__ void stout_store(const SubsweepParams &a, const Pt &x
         vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re, tr_im);
         reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
     }
+    // a rejected link keeps its value: nothing to write in place (annealed),
+    // the old link into the destination when that is another buffer
     if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Un);
+    else if (a.U != a.Usrc) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Ux);
 }
 
 // per-warp reject and FP64-exponential counts

@@ -226,6 +226,25 @@ def test_full_su3_field_parity(ctx, kind, eps):
     assert max_abs(Ug, Uo) < 1e-11
 
 
+@pytest.mark.parametrize("eps,rho", [(-0.25, 0.35), (1.0, 0.75)])
+@pytest.mark.parametrize("n_sweeps", [3, 4])
+def test_simultaneous_vp_with_rejections_fp64(ctx, eps, rho, n_sweeps):
+    """Simultaneous stout smearing (every link from the previous field; the
+    field and a scratch buffer alternate as source and destination) with
+    vortex preservation at steps large enough to reject (the largest the
+    exponential's range check admits for each eps): a rejected link must
+    carry its old value into the destination buffer.  Even and odd sweep
+    counts end in either buffer."""
+    dims = (8, 4, 8, 4)
+    lab = synth.iid_labels(dims, 13)
+    Uo, rej = oracle_pipeline(dims, lab, 0.02, 1234, n_sweeps, rho, eps, schedule=O.SIMULTANEOUS)
+    assert rej.sum() > 0
+    r = gpu_pipeline(vs, ctx, dims, lab, 0.02, 1234, n_sweeps, rho, eps, kind=vs.VS_SIMULTANEOUS)
+    assert [s["n_reject"] for s in r["stats"]] == list(rej)
+    assert max_abs(r["U"], Uo) < 1e-11
+    assert r["check"]["n_label_diff"] == 0
+
+
 @pytest.mark.parametrize("storage,vp", [("link18", True), ("link12", True), ("link18", False)])
 def test_fp32_each_sweep_within_fp32_rounding_of_fp64(ctx, storage, vp):
     """FP32 accuracy along the whole 200-sweep FP64 trajectory.  The annealed
