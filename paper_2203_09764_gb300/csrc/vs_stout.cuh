@@ -375,26 +375,12 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
 }
 
 // ---------------------------------------------------------------------------
-// FP32 over-improved update with the link loads running ahead of the
-// arithmetic.  Each thread keeps the next kRingDepth links it will read in
-// flight as asynchronous global -> shared copies (cp.async) into its own ring
-// of slots, so no register holds a pending load and the latency of one link
-// is covered by the products of the kRingDepth - 1 before it.  A slot is
-// refilled with the link kRingDepth places ahead right after it is read.
-//
-// The wide backward rectangles of link (x, mu) are the wide forward ones of
-// the site below: -mu +nu +mu +mu -nu from x is the path +nu +mu +mu -nu
-// from x - mu, closed by U_mu^dag(x - mu) on the left instead of
-// U_mu^dag(x + mu) on the right.  So with
-//   F(y) = sum_{nu, s} step(y, s nu) U_mu(y + s nu) U_mu(y + s nu + mu) step(y + s nu + 2 mu, -s nu)
-// the rectangle part of Sigma is c1 [F(x) U_mu^dag(x+mu) + U_mu^dag(x-mu) F(x-mu)]
-// and one code body, run with anchor x and x - mu, serves both (each chain
-// multiplied left to right).  Then staples and tall rectangles as in
-// staple_sum.  The 84 + 1 ring links, in order:
-//   F(x), F(x - mu): 4 links per (nu, s), s = +1 then -1, nu = MU+1, MU+2, MU+3
-//   staples + tall:  6 links per (nu, s)
-//   U_mu(x)
-// U_mu(x +- mu) are read with plain loads, one pass ahead of their use.
+// FP32 link streams.  Each thread keeps the next links it will read in flight
+// as asynchronous global -> shared copies (cp.async) into its own ring of
+// slots in shared memory, so no register holds a pending load and the latency
+// of one link is covered by the products of the links before it.  A slot is
+// refilled, right after it is read, with the link that many places ahead in
+// the thread's stream; every slot index is known at compile time.
 // ---------------------------------------------------------------------------
 
 #ifndef VS_RING
@@ -406,27 +392,11 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
 #ifndef VS_RING_MINB
 #define VS_RING_MINB (384 / VS_RING_THREADS)
 #endif
-// depth of the link ring of the stout class kernel: 8 (74 KB of dynamic shared
-// memory per 128-thread block) or 4 (the AUS / APE kernels always use 4)
-#ifndef VS_RING_DEPTH
-#define VS_RING_DEPTH 8
-#endif
-// VS_FUSED: the stout class kernel reads every link of a (nu, s) unit once
-#ifndef VS_FUSED
-#define VS_FUSED 1
-#endif
-
-// VS_TWO_ROW: chains of SU(3) links form only rows 0-1 of each partial product
-#ifndef VS_TWO_ROW
-#define VS_TWO_ROW 1
-#endif
-
-constexpr int kRingDepth = 4;   // the stream patterns below assume 4
 
 template <int NC>
 struct LinkRing {
-    const float4 *v4;   // this thread's column of the float4 slots [kRingDepth][NC/4][BT]
-    const float2 *v2;   // and of the float2 slots [kRingDepth][BT] (NC == 18)
+    const float4 *v4;   // this thread's column of the float4 slots [depth][NC/4][BT]
+    const float2 *v2;   // and of the float2 slots [depth][BT] (NC == 18)
     uint32_t a4, a2;    // the same as shared-window addresses
 };
 
@@ -448,270 +418,6 @@ __device__ __forceinline__ void ring_fetch(const LinkRing<NC> &R, const float *b
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
-
-// Past the end of the stream: an empty group keeps one group per link.
-__device__ __forceinline__ void ring_skip() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-
-// Wait for the link in slot SLOT (all but the kRingDepth - 1 newest groups
-// are complete) and read it, daggered if DAG.
-// FULL = false: only rows 0-1 are needed (a left factor of a two-row
-// product), so 12-real storage skips rebuilding row 2.
-template <int NC, bool DAG, int SLOT, bool FULL = true>
-__device__ __forceinline__ M3<float> ring_read(const LinkRing<NC> &R) {
-    constexpr int NQ = NC / 4;
-    M3<float> m;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const float4 v = R.v4[(SLOT * NQ + q) * VS_RING_THREADS];
-        m.re[2 * q] = v.x; m.im[2 * q] = v.y; m.re[2 * q + 1] = v.z; m.im[2 * q + 1] = v.w;
-    }
-    if (NC == 18) {
-        const float2 v = R.v2[SLOT * VS_RING_THREADS];
-        m.re[8] = v.x; m.im[8] = v.y;
-    }
-    if (NC == 12 && (FULL || DAG)) rebuild_row2(m);
-    return DAG ? m3_dag(m) : m;
-}
-
-template <int NC, bool DAG, int SLOT, bool FULL = true>
-__device__ __forceinline__ M3<float> ring_take(const LinkRing<NC> &R) {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRingDepth - 1) : "memory");
-    return ring_read<NC, DAG, SLOT, FULL>(R);
-}
-
-// Plane-position shifts along mu of the anchor of F: b0, b1, b2 are the
-// shifts to anchor + 0, 1, 2 mu (anchor x: 0, D(1), D(2); anchor x - mu:
-// D(-1), 0, D(1)).
-struct MuOff { int b0, b1, b2; };
-
-// Link K of an F unit (nu, s): K0 = step(y, s nu), K1 = U_mu(y + s nu),
-// K2 = U_mu(y + s nu + mu), K3 = step(y + s nu + 2 mu, -s nu).  A nu-link
-// stepped backwards sits one site further down: the nu offset of the step
-// that starts at y is 0 for s = +1 and -1 for s = -1.
-template <int S, int K>
-__device__ __forceinline__ void f_link(const Around &A, const MuOff &m, const float *Umu, const float *Unu,
-                                       const float *&base, int &pos) {
-    constexpr int a = (K == 0 || K == 3) ? (S > 0 ? 0 : -1) : S;
-    const int dn = around_pos(A, a, 0) - A.i0;
-    const int db = K == 0 || K == 1 ? m.b0 : K == 2 ? m.b1 : m.b2;
-    base = (K == 1 || K == 2) ? Umu : Unu;
-    pos = A.i0 + dn + db;
-}
-
-// Link K of a staple + tall unit (nu, s): K0 = step(x + s nu, s nu),
-// K1 = U_mu(x + 2 s nu), K2 = step(x + 2 s nu + mu, -s nu), K3 = U_mu(x + s nu),
-// K4 = step(x, s nu), K5 = step(x + s nu + mu, -s nu).
-template <int S, int K>
-__device__ __forceinline__ void t_link(const Around &A, const float *Umu, const float *Unu, const float *&base,
-                                       int &pos) {
-    constexpr int a = (K == 0 || K == 2) ? (S > 0 ? 1 : -2) : K == 1 ? 2 * S : K == 3 ? S : (S > 0 ? 0 : -1);
-    constexpr int b = (K == 2 || K == 5) ? 1 : 0;
-    base = (K == 1 || K == 3) ? Umu : Unu;
-    pos = around_pos(A, a, b);
-}
-
-// Stream slots: F units start at multiples of 4; staple units at 48 + 6u.
-template <int S, int K> struct TSlot { static constexpr int v = ((S < 0 ? 2 : 0) + K) & 3; };
-
-// Refill after link K of F unit (nu, s): link K of the next unit, which is
-// (nu, -s) for s = +1; for s = -1 the next nu (An), or after the last nu the
-// first unit of F(x - mu) (mnext) or, after F(x - mu), the first staple unit.
-// The candidates are selected, not branched to.
-template <int NC, int S, int K>
-__device__ __forceinline__ void f_refill(const LinkRing<NC> &R, const float *Umu, const float *Unu,
-                                         const float *Un, long long P, const Around &A, const Around &An,
-                                         const MuOff &m, const MuOff &mnext, bool to_staples) {
-    const float *base;
-    int pos;
-    if constexpr (S > 0) {
-        f_link<-1, K>(A, m, Umu, Unu, base, pos);
-    } else {
-        const float *bt;
-        int pt;
-        f_link<1, K>(An, mnext, Umu, Un, base, pos);
-        t_link<1, K>(An, Umu, Un, bt, pt);
-        base = to_staples ? bt : base;
-        pos = to_staples ? pt : pos;
-    }
-    ring_fetch<NC, K>(R, base, P, pos);
-}
-
-// F += step(y, s nu) U_mu(y + s nu) U_mu(y + s nu + mu) step(y + s nu + 2 mu, -s nu)
-template <int NC, int S>
-__device__ __forceinline__ void f_unit(const LinkRing<NC> &R, M3<float> &F, const float *Umu, const float *Unu,
-                                       const float *Un, long long P, const Around &A, const Around &An,
-                                       const MuOff &m, const MuOff &mnext, bool to_staples) {
-    M3<float> L0 = ring_take<NC, (S < 0), 0, !VS_TWO_ROW>(R);
-    f_refill<NC, S, 0>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-    M3<float> L1 = ring_take<NC, false, 1>(R);
-    f_refill<NC, S, 1>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-    if constexpr (VS_TWO_ROW) {
-        M3<float> W, W2, Y;
-        m3_mul_2r(W, L0, L1);
-        M3<float> L2 = ring_take<NC, false, 2>(R);
-        f_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-        m3_mul_2r(W2, W, L2);
-        M3<float> L3 = ring_take<NC, (S > 0), 3>(R);
-        f_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-        m3_mul_2r(Y, W2, L3);
-        rebuild_row2(Y);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) { F.re[k] += Y.re[k]; F.im[k] += Y.im[k]; }
-    } else {
-        M3<float> W = m3_mul(L0, L1);
-        M3<float> L2 = ring_take<NC, false, 2>(R);
-        f_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-        W = m3_mul(W, L2);
-        M3<float> L3 = ring_take<NC, (S > 0), 3>(R);
-        f_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, m, mnext, to_staples);
-        m3_madd(F, W, L3);
-    }
-}
-
-// Refill after link K of staple unit (nu, s): 4 places ahead in units of 6.
-template <int NC, int S, int K>
-__device__ __forceinline__ void t_refill(const LinkRing<NC> &R, const float *Umu, const float *Unu,
-                                         const float *Un, long long P, const Around &A, const Around &An,
-                                         bool last) {
-    constexpr int SL = TSlot<S, K>::v;
-    const float *base;
-    int pos;
-    if constexpr (K <= 1) {
-        t_link<S, K + 4>(A, Umu, Unu, base, pos);
-        ring_fetch<NC, SL>(R, base, P, pos);
-    } else if constexpr (S > 0) {
-        t_link<-1, K - 2>(A, Umu, Unu, base, pos);
-        ring_fetch<NC, SL>(R, base, P, pos);
-    } else if constexpr (K == 2) {
-        // next nu, or U_mu(x) after the last
-        t_link<1, 0>(An, Umu, Un, base, pos);
-        ring_fetch<NC, SL>(R, last ? Umu : base, P, last ? A.i0 : pos);
-    } else {
-        if (last) {
-            ring_skip();
-        } else {
-            t_link<1, K - 2>(An, Umu, Un, base, pos);
-            ring_fetch<NC, SL>(R, base, P, pos);
-        }
-    }
-}
-
-// Sigma += step(x, s nu) (c0 U_mu(x + s nu) + c1 T) step(x + s nu + mu, -s nu),
-// T = step(x + s nu, s nu) U_mu(x + 2 s nu) step(x + 2 s nu + mu, -s nu)
-template <int NC, int S>
-__device__ __forceinline__ void t_unit(const LinkRing<NC> &R, M3<float> &sig, float c0, float c1,
-                                       const float *Umu, const float *Unu, const float *Un, long long P,
-                                       const Around &A, const Around &An, bool last) {
-    M3<float> T0 = ring_take<NC, (S < 0), TSlot<S, 0>::v, !VS_TWO_ROW>(R);
-    t_refill<NC, S, 0>(R, Umu, Unu, Un, P, A, An, last);
-    M3<float> T1 = ring_take<NC, false, TSlot<S, 1>::v>(R);
-    t_refill<NC, S, 1>(R, Umu, Unu, Un, P, A, An, last);
-    M3<float> Tt;
-    if constexpr (VS_TWO_ROW) {
-        M3<float> T01;
-        m3_mul_2r(T01, T0, T1);
-        M3<float> T2 = ring_take<NC, (S > 0), TSlot<S, 2>::v>(R);
-        t_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
-        m3_mul_2r(Tt, T01, T2);
-        rebuild_row2(Tt);
-    } else {
-        Tt = m3_mul(T0, T1);
-        M3<float> T2 = ring_take<NC, (S > 0), TSlot<S, 2>::v>(R);
-        t_refill<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
-        Tt = m3_mul(Tt, T2);
-    }
-    M3<float> N = ring_take<NC, false, TSlot<S, 3>::v>(R);
-    t_refill<NC, S, 3>(R, Umu, Unu, Un, P, A, An, last);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        N.re[k] = fmaf(c1, Tt.re[k], c0 * N.re[k]);
-        N.im[k] = fmaf(c1, Tt.im[k], c0 * N.im[k]);
-    }
-    M3<float> Af = ring_take<NC, (S < 0), TSlot<S, 4>::v>(R);
-    t_refill<NC, S, 4>(R, Umu, Unu, Un, P, A, An, last);
-    M3<float> AN = m3_mul(Af, N);
-    M3<float> C = ring_take<NC, (S > 0), TSlot<S, 5>::v>(R);
-    t_refill<NC, S, 5>(R, Umu, Unu, Un, P, A, An, last);
-    m3_madd(sig, AN, C);
-}
-
-// Sigma_mu(x) (over-improved, Eq. over-improvement) and U_mu(x) in Ux.
-template <int NC, int MU>
-__device__ __forceinline__ M3<float> staple_sum_ring(const Geo &g, const float *__restrict__ U, Pt x, float c0,
-                                                     float c1, const LinkRing<NC> &R, M3<float> &Ux) {
-    const long long P = g.P;
-    Around A, An;
-    A.i0 = sidx(g, x);
-    A.dmm1 = shift_delta(g, x, MU, -1);
-    A.dmp1 = shift_delta(g, x, MU, 1);
-    A.dmp2 = shift_delta(g, x, MU, 2);
-    An = A;
-    const MuOff m_x = {0, A.dmp1, A.dmp2}, m_xm = {A.dmm1, 0, A.dmp1};
-    const float *Umu = U + (long long)MU * NC * P;
-    const int nu1 = (MU + 1) & 3;
-    around_nu(g, x, nu1, true, A);
-    const float *Unu = U + (long long)nu1 * NC * P;
-    {   // prologue: the first unit of F(x) into slots 0-3
-        const float *b;
-        int q;
-        f_link<1, 0>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 0>(R, b, P, q);
-        f_link<1, 1>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 1>(R, b, P, q);
-        f_link<1, 2>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 2>(R, b, P, q);
-        f_link<1, 3>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 3>(R, b, P, q);
-    }
-    M3<float> sig;
-    m3_zero(sig);
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        // h = 0: c1 F(x) U_mu^dag(x+mu);  h = 1: c1 U_mu^dag(x-mu) F(x-mu)
-        const MuOff m = h ? m_xm : m_x;
-        const M3<float> Lc = load_link<float, NC>(U, P, MU, A.i0 + (h ? A.dmm1 : A.dmp1));
-        M3<float> F;
-        m3_zero(F);
-#pragma unroll 1
-        for (int j = 1; j < 4; ++j) {
-            const bool last = j == 3;
-            const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
-            around_nu(g, x, nun, true, An);
-            const float *Un = U + (long long)nun * NC * P;
-            const MuOff mn = last ? m_xm : m;
-            f_unit<NC, 1>(R, F, Umu, Unu, Un, P, A, An, m, mn, last && h == 1);
-            f_unit<NC, -1>(R, F, Umu, Unu, Un, P, A, An, m, mn, last && h == 1);
-            A = An;
-            Unu = Un;
-        }
-        M3<float> t = h ? m3_mul_dn(Lc, F) : m3_mul_nd(F, Lc);
-        m3_axpy(sig, c1, t);
-    }
-#pragma unroll 1
-    for (int j = 1; j < 4; ++j) {
-        const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
-        around_nu(g, x, nun, true, An);
-        const float *Un = U + (long long)nun * NC * P;
-        t_unit<NC, 1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
-        t_unit<NC, -1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
-        A = An;
-        Unu = Un;
-    }
-    Ux = ring_take<NC, false, 0>(R);
-    return sig;
-}
-
-// ---------------------------------------------------------------------------
-// Depth-8 ring: the same stream with 8 links in flight per thread.  Staple
-// units are padded to 8 stream entries (6 links, 2 empty commit groups), so
-// every slot is the stream index modulo 8 and known at compile time: F units
-// use slots 4 sigma + K (sigma = 1 for s = -1), staple units slots K, U_mu(x)
-// (entry 96) slot 0.  A refill targets the entry 8 ahead: for F units the
-// same (s, K) at the next nu; for staple units (nu, -s) or the next nu.
-// ---------------------------------------------------------------------------
-
-template <int NC, bool DAG, int SLOT, bool FULL = true>
-__device__ __forceinline__ M3<float> ring_take8(const LinkRing<NC> &R) {
-    asm volatile("cp.async.wait_group 7;\n" ::: "memory");
-    return ring_read<NC, DAG, SLOT, FULL>(R);
-}
-
 
 // ring_fetch with a predicate: on == false commits an empty group.
 template <int NC, int SLOT>
@@ -739,194 +445,28 @@ __device__ __forceinline__ void ring_fetch_if(const LinkRing<NC> &R, const float
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Refill after F link K of unit (nu, s): the same link of the next nu (An,
-// mnext); after the last nu of F(x - mu) (to_staples) the staple entry
-// 4 sigma + K of the first staple unit (s = +1), empty for the padding.
-template <int NC, int S, int K>
-__device__ __forceinline__ void f_refill8(const LinkRing<NC> &R, const float *Umu, const float *Un, long long P,
-                                          const Around &An, const MuOff &mnext, bool to_staples) {
-    constexpr int SL = (S < 0 ? 4 : 0) + K;
-    const float *base, *bt;
-    int pos, pt;
-    f_link<S, K>(An, mnext, Umu, Un, base, pos);
-    constexpr int TK = (S < 0 ? 4 : 0) + K;     // staple entry
-    if constexpr (TK <= 5) {
-        t_link<1, (TK <= 5 ? TK : 0)>(An, Umu, Un, bt, pt);
-        ring_fetch<NC, SL>(R, to_staples ? bt : base, P, to_staples ? pt : pos);
-    } else {
-        ring_fetch_if<NC, SL>(R, base, P, pos, !to_staples);
-    }
-}
+// Past the end of the stream: an empty group keeps one group per link.
+__device__ __forceinline__ void ring_skip() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
-// Chains of SU(3) links are SU(3): with VS_TWO_ROW only rows 0-1 of each
-// partial product are formed (m3_mul_2r) and row 2 of the chain is rebuilt
-// as conj(row0 x row1) where a full matrix is needed.
-template <int NC, int S>
-__device__ __forceinline__ void f_unit8(const LinkRing<NC> &R, M3<float> &F, const float *Umu, const float *Un,
-                                        long long P, const Around &An, const MuOff &mnext, bool to_staples) {
-    constexpr int B0 = S < 0 ? 4 : 0;
-    if constexpr (VS_TWO_ROW) {
-        M3<float> L0 = ring_take8<NC, (S < 0), B0 + 0, false>(R);
-        f_refill8<NC, S, 0>(R, Umu, Un, P, An, mnext, to_staples);
-        M3<float> L1 = ring_take8<NC, false, B0 + 1>(R);
-        f_refill8<NC, S, 1>(R, Umu, Un, P, An, mnext, to_staples);
-        M3<float> W;
-        m3_mul_2r(W, L0, L1);
-        M3<float> L2 = ring_take8<NC, false, B0 + 2>(R);
-        f_refill8<NC, S, 2>(R, Umu, Un, P, An, mnext, to_staples);
-        M3<float> W2;
-        m3_mul_2r(W2, W, L2);
-        M3<float> L3 = ring_take8<NC, (S > 0), B0 + 3>(R);
-        f_refill8<NC, S, 3>(R, Umu, Un, P, An, mnext, to_staples);
-        M3<float> Y;
-        m3_mul_2r(Y, W2, L3);
-        rebuild_row2(Y);
+// Read the link in slot SLOT, daggered if DAG; the caller has waited
+// (cp.async.wait_group) until the copy into that slot is complete.
+// FULL = false: only rows 0-1 are needed (a left factor of a two-row
+// product), so 12-real storage skips rebuilding row 2.
+template <int NC, bool DAG, int SLOT, bool FULL = true>
+__device__ __forceinline__ M3<float> ring_read(const LinkRing<NC> &R) {
+    constexpr int NQ = NC / 4;
+    M3<float> m;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) { F.re[k] += Y.re[k]; F.im[k] += Y.im[k]; }
-    } else {
-        M3<float> L0 = ring_take8<NC, (S < 0), B0 + 0>(R);
-        f_refill8<NC, S, 0>(R, Umu, Un, P, An, mnext, to_staples);
-        M3<float> L1 = ring_take8<NC, false, B0 + 1>(R);
-        f_refill8<NC, S, 1>(R, Umu, Un, P, An, mnext, to_staples);
-        M3<float> W = m3_mul(L0, L1);
-        M3<float> L2 = ring_take8<NC, false, B0 + 2>(R);
-        f_refill8<NC, S, 2>(R, Umu, Un, P, An, mnext, to_staples);
-        W = m3_mul(W, L2);
-        M3<float> L3 = ring_take8<NC, (S > 0), B0 + 3>(R);
-        f_refill8<NC, S, 3>(R, Umu, Un, P, An, mnext, to_staples);
-        m3_madd(F, W, L3);
+    for (int q = 0; q < NQ; ++q) {
+        const float4 v = R.v4[(SLOT * NQ + q) * VS_RING_THREADS];
+        m.re[2 * q] = v.x; m.im[2 * q] = v.y; m.re[2 * q + 1] = v.z; m.im[2 * q + 1] = v.w;
     }
-}
-
-// Refill after staple link K of unit (nu, s): s = +1 -> (nu, -1) on A;
-// s = -1 -> (next nu, +1) on An, or after the last nu U_mu(x) (K = 0) and
-// nothing else.
-template <int NC, int S, int K>
-__device__ __forceinline__ void t_refill8(const LinkRing<NC> &R, const float *Umu, const float *Unu,
-                                          const float *Un, long long P, const Around &A, const Around &An,
-                                          bool last) {
-    const float *base;
-    int pos;
-    if constexpr (S > 0) {
-        t_link<-1, K>(A, Umu, Unu, base, pos);
-        ring_fetch<NC, K>(R, base, P, pos);
-    } else {
-        t_link<1, K>(An, Umu, Un, base, pos);
-        if constexpr (K == 0) {
-            ring_fetch<NC, K>(R, last ? Umu : base, P, last ? A.i0 : pos);
-        } else {
-            ring_fetch_if<NC, K>(R, base, P, pos, !last);
-        }
+    if (NC == 18) {
+        const float2 v = R.v2[SLOT * VS_RING_THREADS];
+        m.re[8] = v.x; m.im[8] = v.y;
     }
-}
-
-template <int NC, int S>
-__device__ __forceinline__ void t_unit8(const LinkRing<NC> &R, M3<float> &sig, float c0, float c1,
-                                        const float *Umu, const float *Unu, const float *Un, long long P,
-                                        const Around &A, const Around &An, bool last) {
-    M3<float> T0 = ring_take8<NC, (S < 0), 0, !VS_TWO_ROW>(R);
-    t_refill8<NC, S, 0>(R, Umu, Unu, Un, P, A, An, last);
-    M3<float> T1 = ring_take8<NC, false, 1>(R);
-    t_refill8<NC, S, 1>(R, Umu, Unu, Un, P, A, An, last);
-    M3<float> Tt;
-    if constexpr (VS_TWO_ROW) {
-        M3<float> T01;
-        m3_mul_2r(T01, T0, T1);
-        M3<float> T2 = ring_take8<NC, (S > 0), 2>(R);
-        t_refill8<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
-        m3_mul_2r(Tt, T01, T2);
-        rebuild_row2(Tt);
-    } else {
-        Tt = m3_mul(T0, T1);
-        M3<float> T2 = ring_take8<NC, (S > 0), 2>(R);
-        t_refill8<NC, S, 2>(R, Umu, Unu, Un, P, A, An, last);
-        Tt = m3_mul(Tt, T2);
-    }
-    M3<float> N = ring_take8<NC, false, 3>(R);
-    t_refill8<NC, S, 3>(R, Umu, Unu, Un, P, A, An, last);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        N.re[k] = fmaf(c1, Tt.re[k], c0 * N.re[k]);
-        N.im[k] = fmaf(c1, Tt.im[k], c0 * N.im[k]);
-    }
-    M3<float> Af = ring_take8<NC, (S < 0), 4>(R);
-    t_refill8<NC, S, 4>(R, Umu, Unu, Un, P, A, An, last);
-    M3<float> AN = m3_mul(Af, N);
-    M3<float> C = ring_take8<NC, (S > 0), 5>(R);
-    t_refill8<NC, S, 5>(R, Umu, Unu, Un, P, A, An, last);
-    m3_madd(sig, AN, C);
-    ring_skip();     // padding entries 6, 7: their refills are padding too
-    ring_skip();
-}
-
-template <int NC, int MU>
-__device__ __forceinline__ M3<float> staple_sum_ring8(const Geo &g, const float *__restrict__ U, Pt x, float c0,
-                                                      float c1, const LinkRing<NC> &R, M3<float> &Ux) {
-    const long long P = g.P;
-    Around A, An;
-    A.i0 = sidx(g, x);
-    A.dmm1 = shift_delta(g, x, MU, -1);
-    A.dmp1 = shift_delta(g, x, MU, 1);
-    A.dmp2 = shift_delta(g, x, MU, 2);
-    An = A;
-    const MuOff m_x = {0, A.dmp1, A.dmp2}, m_xm = {A.dmm1, 0, A.dmp1};
-    const float *Umu = U + (long long)MU * NC * P;
-    const int nu1 = (MU + 1) & 3;
-    around_nu(g, x, nu1, true, A);
-    const float *Unu = U + (long long)nu1 * NC * P;
-    {   // prologue: both units of the first nu of F(x) into slots 0-7
-        const float *b;
-        int q;
-        f_link<1, 0>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 0>(R, b, P, q);
-        f_link<1, 1>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 1>(R, b, P, q);
-        f_link<1, 2>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 2>(R, b, P, q);
-        f_link<1, 3>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 3>(R, b, P, q);
-        f_link<-1, 0>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 4>(R, b, P, q);
-        f_link<-1, 1>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 5>(R, b, P, q);
-        f_link<-1, 2>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 6>(R, b, P, q);
-        f_link<-1, 3>(A, m_x, Umu, Unu, b, q); ring_fetch<NC, 7>(R, b, P, q);
-    }
-    M3<float> sig;
-    m3_zero(sig);
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        const MuOff m = h ? m_xm : m_x;
-        const M3<float> Lc = load_link<float, NC>(U, P, MU, A.i0 + (h ? A.dmm1 : A.dmp1));
-        M3<float> F;
-        m3_zero(F);
-#pragma unroll 1
-        for (int j = 1; j < 4; ++j) {
-            const bool last = j == 3;
-            const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
-            around_nu(g, x, nun, true, An);
-            const float *Un = U + (long long)nun * NC * P;
-            const MuOff mn = last ? m_xm : m;
-            f_unit8<NC, 1>(R, F, Umu, Un, P, An, mn, last && h == 1);
-            f_unit8<NC, -1>(R, F, Umu, Un, P, An, mn, last && h == 1);
-            A = An;
-            Unu = Un;
-        }
-        M3<float> t = h ? m3_mul_dn(Lc, F) : m3_mul_nd(F, Lc);
-        m3_axpy(sig, c1, t);
-    }
-#pragma unroll 1
-    for (int j = 1; j < 4; ++j) {
-        const int nun = (MU + (j < 3 ? j + 1 : 1)) & 3;
-        around_nu(g, x, nun, true, An);
-        const float *Un = U + (long long)nun * NC * P;
-        t_unit8<NC, 1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
-        t_unit8<NC, -1>(R, sig, c0, c1, Umu, Unu, Un, P, A, An, j == 3);
-        A = An;
-        Unu = Un;
-    }
-    Ux = ring_take8<NC, false, 0>(R);
-    return sig;
-}
-
-// bytes of dynamic shared memory of the depth-8 ring kernels
-template <int NC>
-constexpr int ring8_smem_bytes() {
-    return 8 * VS_RING_THREADS * ((NC / 4) * 16 + (NC == 18 ? 8 : 0));
+    if (NC == 12 && (FULL || DAG)) rebuild_row2(m);
+    return DAG ? m3_dag(m) : m;
 }
 
 // ---------------------------------------------------------------------------
@@ -1231,45 +771,6 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_fuse
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
         M3<float> sig = staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
-        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
-    }
-    count_update(a, reject, used64);
-}
-
-template <int NC, int MU>
-__global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring8(SubsweepParams a) {
-    extern __shared__ float4 ring8_dyn[];
-    float4 *ring4 = ring8_dyn;
-    float2 *ring2 = reinterpret_cast<float2 *>(ring8_dyn + 8 * (NC / 4) * VS_RING_THREADS);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = t < a.n_threads;
-    bool reject = false, used64 = false;
-    if (active) {
-        const Geo &g = a.g;
-        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
-        const int i = sidx(g, x);
-        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
-        M3<float> Ux;
-        M3<float> sig = staple_sum_ring8<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
-        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
-    }
-    count_update(a, reject, used64);
-}
-
-template <int NC, int MU>
-__global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_ring(SubsweepParams a) {
-    __shared__ float4 ring4[kRingDepth * (NC / 4) * VS_RING_THREADS];
-    __shared__ float2 ring2[NC == 18 ? kRingDepth * VS_RING_THREADS : 1];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = t < a.n_threads;
-    bool reject = false, used64 = false;
-    if (active) {
-        const Geo &g = a.g;
-        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
-        const int i = sidx(g, x);
-        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
-        M3<float> Ux;
-        M3<float> sig = staple_sum_ring<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
         stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
     }
     count_update(a, reject, used64);

@@ -15,7 +15,6 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
         // FP32: the cp.async link-ring kernels
         if (rect) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
-#if VS_FUSED
             constexpr int sm = ring6_smem_bytes<NC>();
             static bool attr_set = false;
             if (!attr_set) {
@@ -31,30 +30,6 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
                 case 2: k_subsweep_fused<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
                 default: k_subsweep_fused<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
             }
-#elif VS_RING_DEPTH == 8
-            constexpr int sm = ring8_smem_bytes<NC>();
-            static bool attr_set = false;
-            if (!attr_set) {
-                cudaFuncSetAttribute(k_subsweep_ring8<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                cudaFuncSetAttribute(k_subsweep_ring8<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                cudaFuncSetAttribute(k_subsweep_ring8<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                cudaFuncSetAttribute(k_subsweep_ring8<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                attr_set = true;
-            }
-            switch (mu) {
-                case 0: k_subsweep_ring8<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
-                case 1: k_subsweep_ring8<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
-                case 2: k_subsweep_ring8<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
-                default: k_subsweep_ring8<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
-            }
-#else
-            switch (mu) {
-                case 0: k_subsweep_ring<NC, 0><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                case 1: k_subsweep_ring<NC, 1><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                case 2: k_subsweep_ring<NC, 2><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-                default: k_subsweep_ring<NC, 3><<<rb, VS_RING_THREADS, 0, st>>>(p); break;
-            }
-#endif
             count_launches(1);
             return cudaGetLastError();
         }
