@@ -274,14 +274,13 @@ cudaError_t launch_ape_tpl(bool rect, int mu, const ApeParams &p, cudaStream_t s
         if (rect) {   // annealed classes and simultaneous sweeps alike
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
             constexpr int sm = ring6_smem_bytes<NC>();
-            static bool attr_set = false;
-            if (!attr_set) {
+            static std::atomic<unsigned long long> attr_set{0};
+            once_per_device(attr_set, [&] {
                 cudaFuncSetAttribute(k_ape_ring<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_ape_ring<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_ape_ring<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_ape_ring<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                attr_set = true;
-            }
+            });
             switch (mu) {
                 case 0: k_ape_ring<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
                 case 1: k_ape_ring<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
@@ -321,8 +320,8 @@ cudaError_t launch_flow_tpl(bool rect, int mu, const FlowParams &p, cudaStream_t
     if constexpr (sizeof(T) == 4 && VS_RING) {
         const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
         constexpr int sm = ring6_smem_bytes<NC>();
-        static bool attr_set = false;
-        if (!attr_set) {
+        static std::atomic<unsigned long long> attr_set{0};
+        once_per_device(attr_set, [&] {
             cudaFuncSetAttribute(k_flow_stage_ring<NC, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             cudaFuncSetAttribute(k_flow_stage_ring<NC, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             cudaFuncSetAttribute(k_flow_stage_ring<NC, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -331,8 +330,7 @@ cudaError_t launch_flow_tpl(bool rect, int mu, const FlowParams &p, cudaStream_t
             cudaFuncSetAttribute(k_flow_stage_ring<NC, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             cudaFuncSetAttribute(k_flow_stage_ring<NC, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             cudaFuncSetAttribute(k_flow_stage_ring<NC, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-            attr_set = true;
-        }
+        });
 #define VS_LAUNCH(R, M) k_flow_stage_ring<NC, R, M><<<rb, VS_RING_THREADS, sm, st>>>(p)
         if (rect) {
             switch (mu) {

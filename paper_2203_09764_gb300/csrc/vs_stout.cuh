@@ -26,6 +26,9 @@
 // |H| <= 1 and needs no eigenvalues, so it has no degeneracy problem.
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include "vs_internal.h"
 
 namespace vs {
@@ -718,6 +721,23 @@ __device__ __forceinline__ M3<float> staple_sum_plain_ring(const Geo &g, const f
     return sig;
 }
 
+// Kernel attributes (here: the dynamic shared memory limit) are set per
+// device.  Runs set() once for each device a launcher is used on; done holds
+// one bit per device ordinal, published after set() has run, so a thread that
+// sees the bit can launch.
+template <class F>
+inline void once_per_device(std::atomic<unsigned long long> &done, F &&set) {
+    int d = 0;
+    cudaGetDevice(&d);
+    const unsigned long long bit = 1ull << (d & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    static std::mutex m;
+    std::lock_guard<std::mutex> lock(m);
+    if (done.load(std::memory_order_relaxed) & bit) return;
+    set();
+    done.fetch_or(bit, std::memory_order_release);
+}
+
 template <int NC>
 constexpr int ring6_smem_bytes() {
     return 6 * VS_RING_THREADS * ((NC / 4) * 16 + (NC == 18 ? 8 : 0));
@@ -896,6 +916,32 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_aus_ring(AusP
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
         const M3<float> Vb = staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.U), x, a.c0_f, a.c1_f, R, Ux);
+        aus_finish<float, NC, MU>(a, x, i, Vb, Ux, reject);
+    }
+    if (a.counters) {
+        unsigned rb = __ballot_sync(0xffffffffu, reject);
+        if ((threadIdx.x & 31) == 0 && rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
+    }
+}
+
+// FP32 AUS + MaxReTr with plaquette staples (eps = 1; alpha = 1 is cooling)
+// through the plaquette-staple ring.
+template <int NC, int MU>
+__global__ void __launch_bounds__(VS_RING_THREADS, 4) k_aus_pring(AusParams a) {
+    extern __shared__ float4 ausp_dyn[];
+    float4 *ring4 = ausp_dyn;
+    float2 *ring2 = reinterpret_cast<float2 *>(ausp_dyn + 6 * (NC / 4) * VS_RING_THREADS);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < a.n_threads;
+    bool reject = false;
+    if (active) {
+        const Geo &g = a.g;
+        const Pt x = class_site<MU>(g, a.colour, t);
+        const int i = sidx(g, x);
+        const float *Us = static_cast<const float *>(a.U);
+        LinkRing<NC> R = ring_of<NC>(ring4, ring2);
+        const M3<float> Vb = staple_sum_plain_ring<NC, MU>(g, Us, x, a.c0_f, R);
+        const M3<float> Ux = load_link<float, NC>(Us, g.P, MU, i);
         aus_finish<float, NC, MU>(a, x, i, Vb, Ux, reject);
     }
     if (a.counters) {

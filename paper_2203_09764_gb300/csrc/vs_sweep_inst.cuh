@@ -16,14 +16,13 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
         if (rect) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
             constexpr int sm = ring6_smem_bytes<NC>();
-            static bool attr_set = false;
-            if (!attr_set) {
+            static std::atomic<unsigned long long> attr_set{0};
+            once_per_device(attr_set, [&] {
                 cudaFuncSetAttribute(k_subsweep_fused<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_subsweep_fused<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_subsweep_fused<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_subsweep_fused<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                attr_set = true;
-            }
+            });
             switch (mu) {
                 case 0: k_subsweep_fused<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
                 case 1: k_subsweep_fused<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
@@ -36,14 +35,13 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
         {   // FP32 plaquette staples (eps = 1): the plaquette-staple link ring
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
             constexpr int sm = ring6_smem_bytes<NC>();
-            static bool attr_set_p = false;
-            if (!attr_set_p) {
+            static std::atomic<unsigned long long> attr_set_p{0};
+            once_per_device(attr_set_p, [&] {
                 cudaFuncSetAttribute(k_subsweep_pring<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_subsweep_pring<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_subsweep_pring<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_subsweep_pring<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                attr_set_p = true;
-            }
+            });
             switch (mu) {
                 case 0: k_subsweep_pring<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
                 case 1: k_subsweep_pring<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
@@ -81,23 +79,41 @@ template <class T, int NC>
 cudaError_t launch_aus_tpl(bool rect, int mu, const AusParams &p, cudaStream_t st) {
     if (p.n_threads <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4 && VS_RING) {
-        // FP32 over-improved staples: the link-ring kernel
+        // FP32: the link-ring kernels
         if (rect) {
             const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
             constexpr int sm = ring6_smem_bytes<NC>();
-            static bool attr_set = false;
-            if (!attr_set) {
+            static std::atomic<unsigned long long> attr_set{0};
+            once_per_device(attr_set, [&] {
                 cudaFuncSetAttribute(k_aus_ring<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_aus_ring<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_aus_ring<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 cudaFuncSetAttribute(k_aus_ring<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                attr_set = true;
-            }
+            });
             switch (mu) {
                 case 0: k_aus_ring<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
                 case 1: k_aus_ring<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
                 case 2: k_aus_ring<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
                 default: k_aus_ring<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+            }
+            count_launches(1);
+            return cudaGetLastError();
+        }
+        {   // FP32 plaquette staples (cooling and eps = 1 AUS): the plaquette-staple ring
+            const int rb = (p.n_threads + VS_RING_THREADS - 1) / VS_RING_THREADS;
+            constexpr int sm = ring6_smem_bytes<NC>();
+            static std::atomic<unsigned long long> attr_set_p{0};
+            once_per_device(attr_set_p, [&] {
+                cudaFuncSetAttribute(k_aus_pring<NC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_aus_pring<NC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_aus_pring<NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                cudaFuncSetAttribute(k_aus_pring<NC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            });
+            switch (mu) {
+                case 0: k_aus_pring<NC, 0><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 1: k_aus_pring<NC, 1><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                case 2: k_aus_pring<NC, 2><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
+                default: k_aus_pring<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
             }
             count_launches(1);
             return cudaGetLastError();
