@@ -9,7 +9,11 @@
 // so the work of all running jobs overlaps on the device and a job that
 // arrives while others run is admitted as soon as a slot and memory free up.
 // Kernels are deterministic and jobs share no device memory, so a job's
-// result does not depend on what else runs.
+// result does not depend on what else runs.  A job runs on a stream whose
+// priority follows its total work (link updates, log scale, smaller work more
+// urgent): the device's block scheduler then serves the short jobs' kernels
+// first, an approximation of shortest-job-first that keeps short jobs from
+// queueing behind long ones.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,7 +51,8 @@ struct Serve {
     std::map<int64_t, std::shared_ptr<Job>> jobs;
     std::deque<int64_t> waiting;
     std::vector<int64_t> running;
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;   // [slot][priority level], level 0 most urgent
+    int n_levels = 1;
     std::vector<bool> slot_busy;
     std::vector<cudaEvent_t> event_pool;
     int64_t next_ticket = 1;
@@ -84,6 +89,15 @@ static uint64_t job_footprint(const vs_job &s) {
     return b;
 }
 
+// Priority level of a job from its work, 4 V (n_sweeps + n_cool) link
+// updates: below 2^24, 2^26, 2^28, and above (0 is the most urgent).
+static int work_level(const vs_job &s, int n_levels) {
+    const double V = (double)s.dims[0] * s.dims[1] * s.dims[2] * s.dims[3];
+    const double w = 4.0 * V * ((double)s.n_sweeps + (double)std::max(s.n_cool, 0));
+    const int lev = w < 16777216.0 ? 0 : w < 67108864.0 ? 1 : w < 268435456.0 ? 2 : 3;
+    return std::min(lev, n_levels - 1);
+}
+
 // Called with the lock held.  Releases it around device work.
 bool Serve::admit_one(std::unique_lock<std::mutex> &lk) {
     if ((int)running.size() >= ctx->opt.max_slots) return false;
@@ -107,7 +121,7 @@ bool Serve::admit_one(std::unique_lock<std::mutex> &lk) {
         auto jp = jobs[t];
         jp->state = RUNNING;
         jp->slot = slot;
-        jp->stream = streams[slot];
+        jp->stream = streams[(size_t)slot * n_levels + work_level(jp->spec, n_levels)];
         jp->result.t_admit_ms = now_ms(ctx);
         bytes_in_use += jp->footprint;
         peak_bytes = std::max(peak_bytes, bytes_in_use);
@@ -285,10 +299,16 @@ static Serve *serve_of(vs_ctx *c) {
         auto s = std::make_unique<Serve>();
         s->ctx = c;
         cudaSetDevice(c->opt.device);
+        int least = 0, greatest = 0;   // numerically: greatest <= least
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+        s->n_levels = std::max(1, std::min(4, least - greatest + 1));
         for (int k = 0; k < c->opt.max_slots; ++k) {
-            cudaStream_t st = nullptr;
-            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-            s->streams.push_back(st);
+            for (int l = 0; l < s->n_levels; ++l) {
+                cudaStream_t st = nullptr;
+                if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest + l) != cudaSuccess)
+                    return nullptr;
+                s->streams.push_back(st);
+            }
             s->slot_busy.push_back(false);
         }
         Serve *raw = s.release();
