@@ -245,6 +245,37 @@ def test_simultaneous_vp_with_rejections_fp64(ctx, eps, rho, n_sweeps):
     assert r["check"]["n_label_diff"] == 0
 
 
+@pytest.mark.parametrize("eps,rho", [(-0.25, 0.35), (1.0, 0.75)])
+def test_fp32_simultaneous_vp_each_sweep(ctx, eps, rho):
+    """FP32 simultaneous stout sweeps with vortex preservation (the link-ring
+    kernels on every link of a direction, writing into the alternate buffer;
+    rejected links carry their old value), each from the oracle's FP64 field,
+    through the sweeps where rejections set in: within 1e-6, with the same
+    decisions except candidates within 1e-5 rad of a sector edge."""
+    dims = (8, 4, 8, 4)
+    lab = synth.iid_labels(dims, 13)
+    U = O.centrifuge(dims, lab, 0.02, 1234)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    worst, ties, n_rej = 0.0, 0, 0
+    for sweep in range(4):
+        vs.vs_load_field(f, links=U)
+        vs.vs_smooth(f, 1, rho, eps, vortex_preserve=True, reunit_every=0, kind=vs.VS_SIMULTANEOUS)
+        Ug = vs.vs_read_field(f)
+        U, rej, cmargin, _ = O.smooth(dims, U, lab, 1, rho, eps=eps, vp=True, schedule=O.SIMULTANEOUS,
+                                      diagnostics=True)
+        n_rej += int(rej.sum())
+        d = np.abs(Ug - U).max(axis=(2, 3))
+        split = d > 1e-4
+        if split.any():
+            assert (cmargin[split] < 1e-5).all(), (sweep, cmargin[split])
+            ties += int(split.sum())
+        worst = max(worst, float(d[~split].max()))
+    vs.vs_field_destroy(f)
+    assert n_rej > 100
+    assert worst < 1e-6
+    assert ties <= 8
+
+
 @pytest.mark.parametrize("storage,vp", [("link18", True), ("link12", True), ("link18", False)])
 def test_fp32_each_sweep_within_fp32_rounding_of_fp64(ctx, storage, vp):
     """FP32 accuracy along the whole 200-sweep FP64 trajectory.  The annealed
