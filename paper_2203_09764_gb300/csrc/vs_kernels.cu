@@ -279,12 +279,14 @@ __device__ __forceinline__ M3<T> clover_F(const Geo &g, const T *__restrict__ U,
     return F;
 }
 
-// Tr(A B) for Hermitian A, B: sum_jk A_jk conj(B_jk), real
+// Tr(A B) for Hermitian A, B: sum_jk A_jk conj(B_jk), real, in the storage
+// precision (its FP32 inputs already carry FP32 rounding; an FP64 dot made the
+// kernel FP64-bound); the sums over sites run in FP64.
 template <class T>
-__device__ __forceinline__ double tr_herm(const M3<T> &A, const M3<T> &B) {
-    double s = 0;
+__device__ __forceinline__ T tr_herm(const M3<T> &A, const M3<T> &B) {
+    T s = T(0);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s += (double)A.re[k] * B.re[k] + (double)A.im[k] * B.im[k];
+    for (int k = 0; k < 9; ++k) s += A.re[k] * B.re[k] + A.im[k] * B.im[k];
     return s;
 }
 
@@ -302,8 +304,8 @@ __global__ void __launch_bounds__(kThreads) k_observables(Geo g, const T *__rest
             const M3<T> Fa = clover_F<T, NC>(g, U, x, i, pairs[pp][0], pairs[pp][1], r1);
             const M3<T> Fb = clover_F<T, NC>(g, U, x, i, pairs[pp][2], pairs[pp][3], r2);
             s += (3.0 - (double)r1) + (3.0 - (double)r2);
-            sr += tr_herm(Fa, Fa) + tr_herm(Fb, Fb);
-            q += sgn[pp] * tr_herm(Fa, Fb);
+            sr += (double)tr_herm(Fa, Fa) + (double)tr_herm(Fb, Fb);
+            q += sgn[pp] * (double)tr_herm(Fa, Fb);
         }
         s *= 2.0 / 72.0;
         sr /= 72.0;
@@ -679,8 +681,19 @@ cudaError_t launch_action(int prec, int nc, const Geo &g, const void *U, double 
 
 cudaError_t launch_observables(int prec, int nc, const Geo &g, const void *U, double *partials, double *out,
                                double *S_site, double *SR_site, double *q_site, cudaStream_t st) {
-    int b = nblocks(g.V);
-    b = b < 400 ? b : 400;
+    // one balanced wave: as many blocks as are resident at once (the kernel's
+    // registers allow one or two per SM), at most 400 (the partials buffer)
+    int b = nblocks(g.V), dev = 0, n_sm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (prec == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_observables<double, 18>, kThreads, 0);
+    else if (nc == 18)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_observables<float, 18>, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_observables<float, 12>, kThreads, 0);
+    const int wave = std::max(1, n_sm * std::max(per_sm, 1));
+    b = std::min(b, std::min(wave, 400));
     if (prec == 0)
         k_observables<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, partials, S_site, SR_site, q_site);
     else if (nc == 18)
