@@ -237,10 +237,16 @@ extern "C" vs_status vs_load_field(vs_field *f, const double *links, const int8_
     CK(cudaSetDevice(f->ctx->opt.device));
     const size_t V = f->g.V;
     if (labels) {
-        if (where == VS_HOST)
-            for (size_t i = 0; i < 4 * V; ++i)
-                if (labels[i] < -1 || labels[i] > 1)
-                    return fail(VS_EINVAL, "vs_load_field: label %d at %zu outside {-1,0,1}", labels[i], i);
+        if (where == VS_HOST) {
+            // branch-free scan (vectorised by the compiler); the position of a
+            // bad label is looked up only when there is one
+            unsigned bad = 0;
+            for (size_t i = 0; i < 4 * V; ++i) bad |= (unsigned)(uint8_t)(labels[i] + 1) > 2u;
+            if (bad)
+                for (size_t i = 0; i < 4 * V; ++i)
+                    if (labels[i] < -1 || labels[i] > 1)
+                        return fail(VS_EINVAL, "vs_load_field: label %d at %zu outside {-1,0,1}", labels[i], i);
+        }
         const int8_t *src = labels;
         if (where == VS_HOST) {
             vs_status st = ensure_scratch(f, 4 * V);
