@@ -101,6 +101,21 @@ def test_load_and_centrifuge_match_oracle(ctx, prec):
         vs.vs_field_destroy(f)
 
 
+def test_load_rejects_host_labels_outside_z3(ctx):
+    """Host labels are checked before any copy: a value outside {-1, 0, 1}
+    anywhere (first or last entry) is VS_EINVAL, naming its position."""
+    dims = (4, 4, 4, 8)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    for pos, val in [(0, 2), (-1, -2)]:
+        lab = synth.iid_labels(dims, 7).copy()
+        lab.reshape(-1)[pos] = val
+        with pytest.raises(vs.VSError) as ei:
+            vs.vs_load_field(f, labels=lab)
+        assert ei.value.status == vs.VS_EINVAL and "outside" in str(ei.value)
+    vs.vs_load_field(f, labels=synth.iid_labels(dims, 7))
+    vs.vs_field_destroy(f)
+
+
 def test_load_links_and_labels_from_fp64_input(ctx):
     dims = (4, 8, 4, 4)
     U = synth.haar_field(dims, 3)
