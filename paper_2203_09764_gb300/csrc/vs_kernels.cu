@@ -366,9 +366,18 @@ __global__ void k_vortex_links(Geo g, const T *__restrict__ U, const int8_t *__r
         int lab = z3_label<T>(a, b);
         cur[(long long)mu * g.P + i] = (int8_t)lab;
         diff = lab != ref[(long long)mu * g.P + i];
-        double arg = atan2((double)b + 0.0, (double)a);
-        const double pi3 = 1.0471975511965976;
-        margin = fmin(fmin(fabs(arg - pi3), fabs(arg + pi3)), 3.141592653589793 - fabs(arg));
+        // angular distance of arg Tr U from the nearest sector edge (+-pi/3,
+        // pi), in the field's precision: an FP32 trace is itself rounded to
+        // ~1e-7, and an FP64 atan2 per link made this kernel FP64-bound
+        if constexpr (sizeof(T) == 4) {
+            const float argf = atan2f(b + 0.0f, a);
+            const float pi3f = 1.04719755f;
+            margin = (double)fminf(fminf(fabsf(argf - pi3f), fabsf(argf + pi3f)), 3.14159265f - fabsf(argf));
+        } else {
+            double arg = atan2((double)b + 0.0, (double)a);
+            const double pi3 = 1.0471975511965976;
+            margin = fmin(fmin(fabs(arg - pi3), fabs(arg + pi3)), 3.141592653589793 - fabs(arg));
+        }
         near = margin < 1e-5;
     }
     count_warp(&counts[0], diff);
