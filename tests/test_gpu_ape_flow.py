@@ -67,10 +67,11 @@ def test_ucp_smoothing_fp64_matches_oracle(ctx, case):
         assert chk["n_label_diff"] == 0 and chk["n_charge_diff"] == 0
 
 
-@pytest.mark.parametrize("storage", ["link18", "link12"])
-def test_ucp_fp32_each_sweep_within_rounding(ctx, storage):
-    """FP32 AUS+UCP from the oracle's FP64 state, one sweep at a time."""
-    dims = (8, 8, 8, 8)
+@pytest.mark.parametrize("storage,dims", [("link18", (8, 8, 8, 8)), ("link12", (8, 8, 8, 8)),
+                                          ("link18", (4, 4, 12, 20))])
+def test_ucp_fp32_each_sweep_within_rounding(ctx, storage, dims):
+    """FP32 AUS+UCP from the oracle's FP64 state, one sweep at a time (also on
+    a lattice whose class launches end in a partial block)."""
     lab = cooled_labels(dims, 2)
     G = synth.random_gauge(dims, 46)
     U = O.gauge_transform(dims, O.centrifuge(dims, lab, 0.02, 1234), G)
@@ -85,6 +86,29 @@ def test_ucp_fp32_each_sweep_within_rounding(ctx, storage):
         worst = max(worst, max_abs(Ug, U))
     vs.vs_field_destroy(f)
     assert worst < 3e-6
+
+
+def test_ape_simultaneous_fp32_each_sweep_within_rounding(ctx):
+    """FP32 APE smearing with UCP (simultaneous: every link from the previous
+    field, through the alternate buffer) on a randomly gauged field, one sweep
+    at a time from the oracle's FP64 state, at the benchmark's alpha = 0.5.
+    The FP32 projection (Newton polar iteration stopped at a squared step of
+    1e-13, adjugate inverse, cube root of the determinant) leaves a few 1e-6
+    per sweep at this blocking weight: measured 7.6e-6, and 7.4e-6 with plain
+    loads and a field copy per sweep; 1.5e-5."""
+    dims = (8, 8, 8, 8)
+    lab = cooled_labels(dims, 2)
+    U = O.gauge_transform(dims, O.centrifuge(dims, lab, 0.02, 1234), synth.random_gauge(dims, 47))
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    worst = 0.0
+    for _ in range(5):
+        vs.vs_load_field(f, links=U)
+        vs.vs_smooth_ape(f, 1, 0.5, -0.25, vortex_preserve=False, reunit_every=0, schedule=vs.VS_SIMULTANEOUS)
+        Ug = vs.vs_read_field(f)
+        U, _ = O.ape_ucp(dims, U, None, 1, 0.5, eps=-0.25, schedule="simultaneous", vp=False)
+        worst = max(worst, max_abs(Ug, U))
+    vs.vs_field_destroy(f)
+    assert worst < 1.5e-5
 
 
 def test_ucp_keeps_a_vortex_field_on_centre_elements(ctx):

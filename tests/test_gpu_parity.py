@@ -475,12 +475,17 @@ def test_aus_cooling_equals_hot_start_generator_step(ctx):
     assert max_abs(Ug, O.cool(dims, U, 2)) < 1e-12
 
 
-@pytest.mark.parametrize("eps", [-0.25, 1.0])
-def test_aus_fp32_each_sweep_within_rounding(ctx, eps):
-    dims = (8, 8, 8, 8)
+@pytest.mark.parametrize("eps,storage,dims", [(-0.25, "link18", (8, 8, 8, 8)), (1.0, "link18", (8, 8, 8, 8)),
+                                              (-0.25, "link12", (8, 8, 8, 8)), (-0.25, "link18", (4, 4, 12, 20))])
+def test_aus_fp32_each_sweep_within_rounding(ctx, eps, storage, dims):
+    """FP32 AUS + MaxReTr with VP on a centrifuged vortex field, one sweep at a
+    time from the oracle's FP64 field (18- and 12-real storage; 4x4x12x20 ends
+    every class launch in a partial block).  1e-6; 2e-6 for 12-real storage,
+    which rebuilds row 2 of every link it reads and of the result (measured
+    1.04e-6, the same with plain loads as with the link ring)."""
     lab = cooled_labels(dims, 2)
     U = O.centrifuge(dims, lab, 0.02, 1234)
-    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12)
     worst = 0.0
     for sweep in range(30):
         vs.vs_load_field(f, links=U)
@@ -489,7 +494,7 @@ def test_aus_fp32_each_sweep_within_rounding(ctx, eps):
         U, _ = O.aus(dims, U, lab, 1, 0.02, eps=eps, vp=True)
         worst = max(worst, max_abs(Ug, U))
     vs.vs_field_destroy(f)
-    assert worst < 1e-6
+    assert worst < (1e-6 if storage == "link18" else 2e-6)
 
 
 @pytest.mark.parametrize("storage", ["link18", "link12"])
