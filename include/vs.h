@@ -258,6 +258,23 @@ vs_status vs_action(vs_field *f, double *mean_S);
 /* Copy out the current links (FP64, host layout above) or labels. */
 vs_status vs_read_field(vs_field *f, double *links_out, int32_t where);
 vs_status vs_read_labels(vs_field *f, int8_t *labels_out, int32_t where);     /* reference */
+
+/* Checkpoint and resume (not in the paper).  vs_field_checkpoint writes the
+ * links (FP64 [4][V][3][3] complex, as vs_read_field), the reference labels
+ * (int8 [4][V], as vs_read_labels) and the number of sweeps since the last
+ * load (it sets the phase of the periodic re-unitarisation) to caller-owned
+ * buffers on the host or the device (`where`); synchronous for the host.
+ * vs_field_restore loads them into a field of the same dims, precision and
+ * storage.  The kernels are deterministic, so N + M sweeps equal N sweeps,
+ * checkpoint, restore into any field, then M sweeps, bit for bit (FP32 links
+ * are exact in FP64; 12-real storage rebuilds row 2 the same way).
+ * EINVAL: NULL buffers, a field not loaded, sweeps_done < 0, host labels
+ * outside {-1, 0, 1}; EUNSUPPORTED: a field in a random gauge (checkpoint
+ * before vs_gauge_transform). */
+vs_status vs_field_checkpoint(vs_field *f, double *links_out, int8_t *labels_out, int64_t *sweeps_done,
+                              int32_t where);
+vs_status vs_field_restore(vs_field *f, const double *links, const int8_t *labels, int64_t sweeps_done,
+                           int32_t where);
 vs_status vs_current_labels(vs_field *f, int8_t *labels_out, int32_t where);  /* of current links */
 
 /* Random gauge transformation (Sec. V.D): U_mu(x) -> G(x) U_mu(x) G^dag(x+mu)

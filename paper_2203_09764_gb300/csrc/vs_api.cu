@@ -229,6 +229,18 @@ extern "C" vs_status vs_synchronize(vs_field *f) {
 // Load / read
 // ---------------------------------------------------------------------------
 
+// Host labels outside {-1, 0, 1} are rejected (branch-free scan, the
+// position looked up only when there is a bad one).
+static vs_status check_host_labels(const int8_t *labels, size_t n, const char *what) {
+    unsigned bad = 0;
+    for (size_t i = 0; i < n; ++i) bad |= (unsigned)(uint8_t)(labels[i] + 1) > 2u;
+    if (bad)
+        for (size_t i = 0; i < n; ++i)
+            if (labels[i] < -1 || labels[i] > 1)
+                return fail(VS_EINVAL, "%s: label %d at %zu outside {-1,0,1}", what, labels[i], i);
+    return VS_OK;
+}
+
 extern "C" vs_status vs_load_field(vs_field *f, const double *links, const int8_t *labels, int32_t where) {
     if (!f) return fail(VS_EINVAL, "vs_load_field: NULL field");
     if ((links == nullptr) == (labels == nullptr))
@@ -238,14 +250,8 @@ extern "C" vs_status vs_load_field(vs_field *f, const double *links, const int8_
     const size_t V = f->g.V;
     if (labels) {
         if (where == VS_HOST) {
-            // branch-free scan (vectorised by the compiler); the position of a
-            // bad label is looked up only when there is one
-            unsigned bad = 0;
-            for (size_t i = 0; i < 4 * V; ++i) bad |= (unsigned)(uint8_t)(labels[i] + 1) > 2u;
-            if (bad)
-                for (size_t i = 0; i < 4 * V; ++i)
-                    if (labels[i] < -1 || labels[i] > 1)
-                        return fail(VS_EINVAL, "vs_load_field: label %d at %zu outside {-1,0,1}", labels[i], i);
+            vs_status st = check_host_labels(labels, 4 * V, "vs_load_field");
+            if (st) return st;
         }
         const int8_t *src = labels;
         if (where == VS_HOST) {
@@ -269,6 +275,44 @@ extern "C" vs_status vs_load_field(vs_field *f, const double *links, const int8_
     f->loaded = true;
     f->sweeps_done = 0;
     f->gauge_on = false;
+    return VS_OK;
+}
+
+extern "C" vs_status vs_field_checkpoint(vs_field *f, double *links_out, int8_t *labels_out, int64_t *sweeps_done,
+                                         int32_t where) {
+    if (!f || !links_out || !labels_out || !sweeps_done) return fail(VS_EINVAL, "vs_field_checkpoint: NULL argument");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_field_checkpoint: field not loaded");
+    if (f->gauge_on)
+        return fail(VS_EUNSUPPORTED, "vs_field_checkpoint: the field is in a random gauge (checkpoint before "
+                                     "vs_gauge_transform)");
+    vs_status st = vs_read_field(f, links_out, where);
+    if (st) return st;
+    if ((st = vs_read_labels(f, labels_out, where))) return st;
+    *sweeps_done = f->sweeps_done;
+    return VS_OK;
+}
+
+extern "C" vs_status vs_field_restore(vs_field *f, const double *links, const int8_t *labels, int64_t sweeps_done,
+                                      int32_t where) {
+    if (!f || !links || !labels) return fail(VS_EINVAL, "vs_field_restore: NULL argument");
+    if (sweeps_done < 0) return fail(VS_EINVAL, "vs_field_restore: sweeps_done < 0");
+    if (where != VS_HOST && where != VS_DEVICE) return fail(VS_EINVAL, "vs_field_restore: bad `where`");
+    const size_t V = f->g.V;
+    if (where == VS_HOST) {
+        vs_status st = check_host_labels(labels, 4 * V, "vs_field_restore");
+        if (st) return st;
+    }
+    vs_status st = vs_load_field(f, links, nullptr, where);   // links; labels recomputed, then replaced
+    if (st) return st;
+    const int8_t *src = labels;
+    if (where == VS_HOST) {
+        if ((st = ensure_scratch(f, 4 * V))) return st;
+        CK(cudaMemcpyAsync(f->scratch, labels, 4 * V, cudaMemcpyHostToDevice, f->stream));
+        src = (const int8_t *)f->scratch;
+    }
+    CK(launch_store_ref(f->g, src, f->ref, f->stream));
+    if (where == VS_HOST) CK(cudaStreamSynchronize(f->stream));
+    f->sweeps_done = sweeps_done;
     return VS_OK;
 }
 

@@ -96,6 +96,14 @@ __global__ void k_read_labels(Geo g, const int8_t *__restrict__ ref, int8_t *out
     out[l] = ref[(long long)mu * g.P + sidx(g, site_of_lex(g, s))];
 }
 
+// reference labels from lexicographic order into plane order (restore)
+__global__ void k_store_ref(Geo g, const int8_t *__restrict__ lab, int8_t *ref) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4ll * g.V) return;
+    int mu = (int)(l / g.V), s = (int)(l % g.V);
+    ref[(long long)mu * g.P + sidx(g, site_of_lex(g, s))] = lab[l];
+}
+
 template <class T, int NC>
 __global__ void k_current_labels(Geo g, const T *__restrict__ U, int8_t *out) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -642,6 +650,12 @@ cudaError_t launch_read_links(int prec, int nc, const Geo &g, const void *U, dou
     if (prec == 0) k_read_links<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, out);
     else if (nc == 18) k_read_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
     else k_read_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_ref(const Geo &g, const int8_t *lab_lex, int8_t *ref, cudaStream_t st) {
+    k_store_ref<<<nblocks(4ll * g.V), kThreads, 0, st>>>(g, lab_lex, ref);
     count_launches(1);
     return cudaGetLastError();
 }

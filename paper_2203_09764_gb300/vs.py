@@ -122,6 +122,8 @@ _SIGS = {
     "vs_observables": (ctypes.c_int32, [P, ctypes.POINTER(vs_observables_out), P, P, P, ctypes.c_int32]),
     "vs_read_field": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_read_labels": (ctypes.c_int32, [P, P, ctypes.c_int32]),
+    "vs_field_checkpoint": (ctypes.c_int32, [P, P, P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    "vs_field_restore": (ctypes.c_int32, [P, P, P, ctypes.c_int64, ctypes.c_int32]),
     "vs_current_labels": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_reunitarise": (ctypes.c_int32, [P]),
     "vs_gauge_transform": (ctypes.c_int32, [P, P, ctypes.c_int32]),
@@ -411,6 +413,37 @@ def vs_read_field(f, out=None):
     p, where = _ptr(out)
     _check(lib.vs_read_field(f, p, where))
     return out
+
+
+def vs_field_checkpoint(f, links_out=None, labels_out=None):
+    """(links, reference labels, sweeps_done) of a field: host numpy arrays, or
+    the caller's buffers (both numpy or both torch CUDA)."""
+    V = _field_sites(f)
+    if links_out is None:
+        links_out = np.empty((4, V, 3, 3), dtype=np.complex128)
+    if labels_out is None:
+        labels_out = np.empty((4, V), dtype=np.int8)
+    pl, where = _ptr(links_out)
+    pn, where2 = _ptr(labels_out)
+    if where != where2:
+        raise ValueError("links_out and labels_out must both be host or both device buffers")
+    n = ctypes.c_int64(0)
+    _check(lib.vs_field_checkpoint(f, pl, pn, ctypes.byref(n), where))
+    return links_out, labels_out, int(n.value)
+
+
+def vs_field_restore(f, links, labels, sweeps_done):
+    """Load a checkpoint (as vs_field_checkpoint returns it) into a field of the
+    same dims, precision and storage."""
+    if isinstance(links, np.ndarray):
+        links = np.ascontiguousarray(links, dtype=np.complex128)
+    if isinstance(labels, np.ndarray):
+        labels = np.ascontiguousarray(labels, dtype=np.int8)
+    pl, where = _ptr(links)
+    pn, where2 = _ptr(labels)
+    if where != where2:
+        raise ValueError("links and labels must both be host or both device buffers")
+    _check(lib.vs_field_restore(f, pl, pn, int(sweeps_done), where))
 
 
 def vs_read_labels(f, out=None):

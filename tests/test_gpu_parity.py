@@ -116,6 +116,53 @@ def test_load_rejects_host_labels_outside_z3(ctx):
     vs.vs_field_destroy(f)
 
 
+@pytest.mark.parametrize("prec,storage", [("fp32", "link18"), ("fp32", "link12"), ("fp64", "link18")])
+def test_checkpoint_restore_resumes_bit_for_bit(ctx, prec, storage):
+    """N + M sweeps equal N sweeps, checkpoint, restore into another field,
+    M sweeps: bit for bit, across a re-unitarisation (every 4 sweeps, N = 3,
+    M = 6), with VP against the original reference labels (restored as given,
+    not recomputed from the links)."""
+    dims = (4, 8, 4, 8)
+    lab = cooled_labels(dims, 2)
+    p = vs.VS_FP64 if prec == "fp64" else vs.VS_FP32
+    st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
+
+    def fresh():
+        f = vs.vs_field_create(ctx, dims, p, st)
+        vs.vs_load_field(f, labels=lab)
+        vs.vs_centrifuge(f, 0.02, 1234)
+        return f
+
+    a = fresh()
+    ra = vs.vs_smooth(a, 9, 0.06, -0.25, reunit_every=4, stats=True)
+    Ua = vs.vs_read_field(a)
+    vs.vs_field_destroy(a)
+    b = fresh()
+    rb = vs.vs_smooth(b, 3, 0.06, -0.25, reunit_every=4, stats=True)
+    links, labels, n = vs.vs_field_checkpoint(b)
+    vs.vs_field_destroy(b)
+    assert n == 3 and np.array_equal(labels, lab)
+    c = vs.vs_field_create(ctx, dims, p, st)
+    vs.vs_field_restore(c, links, labels, n)
+    rc = vs.vs_smooth(c, 6, 0.06, -0.25, reunit_every=4, stats=True)
+    Uc = vs.vs_read_field(c)
+    assert np.array_equal(vs.vs_read_labels(c), lab)
+    vs.vs_field_destroy(c)
+    assert np.array_equal(Ua, Uc)
+    assert [s["n_reject"] for s in ra] == [s["n_reject"] for s in rb + rc]
+
+
+def test_checkpoint_refuses_gauge_transformed_fields(ctx):
+    dims = (4, 4, 4, 4)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=synth.iid_labels(dims, 3))
+    vs.vs_gauge_transform(f, synth.random_gauge(dims, 4))
+    with pytest.raises(vs.VSError) as ei:
+        vs.vs_field_checkpoint(f)
+    assert ei.value.status == vs.VS_EUNSUPPORTED
+    vs.vs_field_destroy(f)
+
+
 def test_load_links_and_labels_from_fp64_input(ctx):
     dims = (4, 8, 4, 4)
     U = synth.haar_field(dims, 3)
