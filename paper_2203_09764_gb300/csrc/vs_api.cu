@@ -569,6 +569,7 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
     // last sweep wrote the scratch buffer.
     void *cur = f->U, *nxt = f->scratch;
     for (int s = 0; s < n_sweeps; ++s) {
+        NvtxRange range("vs stout sweep");
         const double r = a.rho_per_sweep ? a.rho_per_sweep[s] : rho;
         SubsweepParams p = make_params(f, r, eps, u0, vp);
         p.counters = fixed_counters ? fixed_counters : (want_stats ? f->sweep_counts + 2 * s : nullptr);
@@ -667,6 +668,7 @@ extern "C" vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, 
         CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_sweeps, f->stream));
     AusParams a = make_aus_params(f, alpha, epsilon, u0, n_hits, vortex_preserve);
     for (int s = 0; s < n_sweeps; ++s) {
+        NvtxRange range("vs AUS sweep");
         a.counters = stats ? f->sweep_counts + 2 * s : nullptr;
         for (int mu = 0; mu < 4; ++mu)
             for (int c = 0; c < 4; ++c) {
@@ -757,6 +759,7 @@ extern "C" vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, 
     a.vp = vortex_preserve ? 1 : 0;
     void *cur = f->U, *nxt = f->scratch;   // simultaneous: alternating buffers, as in vs_smooth
     for (int s = 0; s < n_sweeps; ++s) {
+        NvtxRange range("vs APE/UCP sweep");
         a.counters = stats ? f->sweep_counts + 2 * s : nullptr;
         if (schedule == VS_ANNEALED) {
             a.U = f->U;
@@ -843,6 +846,7 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
     // stage wrote the scratch buffer.
     void *cur = f->U, *nxt = f->scratch;
     for (int s = 0; s < n_steps; ++s) {
+        NvtxRange range("vs RK3 step");
         p.counters = stats ? f->sweep_counts + 2 * s : nullptr;
         for (int k = 0; k < 3; ++k) {
             p.a = A[k];

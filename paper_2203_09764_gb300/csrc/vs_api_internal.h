@@ -13,6 +13,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/vs.h"
 #include "vs_internal.h"
@@ -60,6 +61,15 @@ struct vs_field {
 };
 
 namespace vs {
+
+// NVTX range for tools such as Nsight Systems (header-only NVTX v3: a no-op
+// unless a tool is attached to the process).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 vs_status fail(vs_status st, const char *fmt, ...);
 vs_status cuda_fail(cudaError_t e, const char *what);

@@ -175,6 +175,7 @@ void Serve::finish(Job &j, vs_status st) {
 
 // Enqueue the next chunk of a running job (lock released by caller).
 static vs_status enqueue_chunk(Job &j, unsigned long long *ctr) {
+    NvtxRange range("vs served chunk");
     vs_field *f = j.f;
     const vs_job &s = j.spec;
     int left = s.n_sweeps - j.sweeps_enqueued;
