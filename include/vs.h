@@ -259,6 +259,10 @@ vs_status vs_action(vs_field *f, double *mean_S);
 vs_status vs_read_field(vs_field *f, double *links_out, int32_t where);
 vs_status vs_read_labels(vs_field *f, int8_t *labels_out, int32_t where);     /* reference */
 
+/* Number of links with a NaN or Inf entry (a guard for diverging or singular
+ * updates; 0 for every workload).  Synchronous. */
+vs_status vs_field_count_nonfinite(vs_field *f, int64_t *n_links);
+
 /* Checkpoint and resume (not in the paper).  vs_field_checkpoint writes the
  * links (FP64 [4][V][3][3] complex, as vs_read_field), the reference labels
  * (int8 [4][V], as vs_read_labels) and the number of sweeps since the last

@@ -278,6 +278,19 @@ extern "C" vs_status vs_load_field(vs_field *f, const double *links, const int8_
     return VS_OK;
 }
 
+extern "C" vs_status vs_field_count_nonfinite(vs_field *f, int64_t *n_links) {
+    if (!f || !n_links) return fail(VS_EINVAL, "vs_field_count_nonfinite: NULL argument");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_field_count_nonfinite: field not loaded");
+    CK(cudaSetDevice(f->ctx->opt.device));
+    unsigned long long *cnt = f->d_counts + 7, h = 0;
+    CK(cudaMemsetAsync(cnt, 0, sizeof h, f->stream));
+    CK(launch_count_nonfinite(f->prec == VS_FP32, f->nc, f->g, f->U, cnt, f->stream));
+    CK(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    *n_links = (int64_t)h;
+    return VS_OK;
+}
+
 extern "C" vs_status vs_field_checkpoint(vs_field *f, double *links_out, int8_t *labels_out, int64_t *sweeps_done,
                                          int32_t where) {
     if (!f || !links_out || !labels_out || !sweeps_done) return fail(VS_EINVAL, "vs_field_checkpoint: NULL argument");

@@ -98,6 +98,8 @@ cudaError_t launch_read_links(int prec, int nc, const Geo &g, const void *U, dou
                               cudaStream_t st);
 cudaError_t launch_read_labels(const Geo &g, const int8_t *ref, int8_t *out_lex, cudaStream_t st);
 cudaError_t launch_store_ref(const Geo &g, const int8_t *lab_lex, int8_t *ref, cudaStream_t st);
+cudaError_t launch_count_nonfinite(int prec, int nc, const Geo &g, const void *U, unsigned long long *count,
+                                   cudaStream_t st);
 cudaError_t launch_current_labels(int prec, int nc, const Geo &g, const void *U, int8_t *out_lex,
                                   cudaStream_t st);
 cudaError_t launch_centrifuge(int prec, int nc, const Geo &g, const int8_t *ref, double omega,

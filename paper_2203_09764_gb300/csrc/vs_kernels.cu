@@ -96,6 +96,20 @@ __global__ void k_read_labels(Geo g, const int8_t *__restrict__ ref, int8_t *out
     out[l] = ref[(long long)mu * g.P + sidx(g, site_of_lex(g, s))];
 }
 
+// Links with a non-finite entry (NaN or Inf), one thread per link.
+template <class T, int NC>
+__global__ void k_count_nonfinite(Geo g, const T *__restrict__ U, unsigned long long *count) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (l < 4ll * g.V) {
+        const M3<T> m = load_link<T, NC>(U, g.P, (int)(l / g.V), (int)(l % g.V));
+#pragma unroll
+        for (int k = 0; k < 9; ++k) bad |= !isfinite(m.re[k]) || !isfinite(m.im[k]);
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, (unsigned long long)__popc(b));
+}
+
 // reference labels from lexicographic order into plane order (restore)
 __global__ void k_store_ref(Geo g, const int8_t *__restrict__ lab, int8_t *ref) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -650,6 +664,16 @@ cudaError_t launch_read_links(int prec, int nc, const Geo &g, const void *U, dou
     if (prec == 0) k_read_links<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, out);
     else if (nc == 18) k_read_links<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
     else k_read_links<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_nonfinite(int prec, int nc, const Geo &g, const void *U, unsigned long long *count,
+                                   cudaStream_t st) {
+    const int b = nblocks(4ll * g.V);
+    if (prec == 0) k_count_nonfinite<double, 18><<<b, kThreads, 0, st>>>(g, (const double *)U, count);
+    else if (nc == 18) k_count_nonfinite<float, 18><<<b, kThreads, 0, st>>>(g, (const float *)U, count);
+    else k_count_nonfinite<float, 12><<<b, kThreads, 0, st>>>(g, (const float *)U, count);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -122,6 +122,7 @@ _SIGS = {
     "vs_observables": (ctypes.c_int32, [P, ctypes.POINTER(vs_observables_out), P, P, P, ctypes.c_int32]),
     "vs_read_field": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_read_labels": (ctypes.c_int32, [P, P, ctypes.c_int32]),
+    "vs_field_count_nonfinite": (ctypes.c_int32, [P, ctypes.POINTER(ctypes.c_int64)]),
     "vs_field_checkpoint": (ctypes.c_int32, [P, P, P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "vs_field_restore": (ctypes.c_int32, [P, P, P, ctypes.c_int64, ctypes.c_int32]),
     "vs_current_labels": (ctypes.c_int32, [P, P, ctypes.c_int32]),
@@ -413,6 +414,13 @@ def vs_read_field(f, out=None):
     p, where = _ptr(out)
     _check(lib.vs_read_field(f, p, where))
     return out
+
+
+def vs_field_count_nonfinite(f):
+    """Number of links with a NaN or Inf entry."""
+    n = ctypes.c_int64(0)
+    _check(lib.vs_field_count_nonfinite(f, ctypes.byref(n)))
+    return int(n.value)
 
 
 def vs_field_checkpoint(f, links_out=None, labels_out=None):

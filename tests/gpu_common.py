@@ -36,6 +36,7 @@ def gpu_pipeline(vs, ctx, dims, labels, omega, cseed, n_sweeps, rho, eps, vp=Tru
             vs.vs_centrifuge(f, omega, cseed)
         stats = vs.vs_smooth(f, n_sweeps, rho, eps, vortex_preserve=vp, stats=True,
                              reunit_every=reunit_every, kind=kind)
+        assert vs.vs_field_count_nonfinite(f) == 0
         U = vs.vs_read_field(f)
         cur = vs.vs_current_labels(f)
         S = vs.vs_action(f)

@@ -152,6 +152,26 @@ def test_checkpoint_restore_resumes_bit_for_bit(ctx, prec, storage):
     assert [s["n_reject"] for s in ra] == [s["n_reject"] for s in rb + rc]
 
 
+@pytest.mark.parametrize("prec,storage", [("fp32", "link18"), ("fp32", "link12"), ("fp64", "link18")])
+def test_nonfinite_links_are_counted(ctx, prec, storage):
+    """The NaN/Inf guard counts exactly the links that carry a non-finite
+    entry (in a row that the storage keeps), and none on a smoothed field."""
+    dims = (4, 4, 4, 8)
+    U = O.cool(dims, synth.haar_field(dims, 5), 1)
+    p = vs.VS_FP64 if prec == "fp64" else vs.VS_FP32
+    f = vs.vs_field_create(ctx, dims, p, vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12)
+    vs.vs_load_field(f, links=U)
+    vs.vs_smooth(f, 2, 0.06, -0.25, vortex_preserve=False)
+    assert vs.vs_field_count_nonfinite(f) == 0
+    bad = U.copy()
+    bad[0, 3, 0, 1] = np.nan
+    bad[2, 17, 1, 2] = np.inf
+    bad[3, 40, 0, 0] = complex(0.0, -np.inf)
+    vs.vs_load_field(f, links=bad)
+    assert vs.vs_field_count_nonfinite(f) == 3
+    vs.vs_field_destroy(f)
+
+
 def test_checkpoint_refuses_gauge_transformed_fields(ctx):
     dims = (4, 4, 4, 4)
     f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
