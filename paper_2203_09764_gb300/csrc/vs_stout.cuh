@@ -1,4 +1,5 @@
-// vs_stout.cuh -- staple sums, stout candidate and the colour-class update kernel.
+// vs_stout.cuh -- staple sums (plain loads, the one-pass link stream, the plaquette-staple
+// stream), the stout candidate, and the colour-class update and AUS kernels.
 //
 // Stout step, Sec. II.A Eqs. (stout)/(generator):
 //   Omega = Sigma U^dag,  Q = (Omega - Omega^dag)/2 - Tr(Omega - Omega^dag)/6,
