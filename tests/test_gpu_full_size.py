@@ -11,11 +11,14 @@ the launch (its own staple sum, generator and exponential) and the
 vortex-preservation decision.  Links outside the class must be untouched.
 """
 
+import functools
+
 import numpy as np
 import pytest
 
 import oracle as O
 from tests import lattice_np as L
+from tests.gpu_common import cooled_labels
 
 pytestmark = pytest.mark.gpu
 
@@ -156,3 +159,114 @@ def test_sampled_ape_simultaneous_at_full_size():
             if cand is None:
                 cand = U[mu, s]
             assert np.abs(U1[mu, s] - cand).max() < 1.5e-5
+
+
+# Every link at full size: the field is an 8^4 field repeated periodically over
+# 32^3 x 64.  The colour classes c_mu(x) repeat with period 4 in every direction
+# and the schedules treat all sites alike, so the exact result is the oracle's
+# 8^4 result repeated; the kernels see 32^3 x 64 with the benchmark's launch
+# shapes and distinct coordinates everywhere, and a neighbour index that went
+# wrong anywhere would break the repetition.
+TILE = (8, 8, 8, 8)
+FULL = (32, 32, 32, 64)
+REPS = tuple(F // T for F, T in zip(FULL, TILE))
+
+
+def _tile(a):
+    inner = a.shape[2:]
+    t = a.reshape((4,) + TILE[::-1] + inner)
+    return np.tile(t, (1,) + REPS[::-1] + (1,) * len(inner)).reshape((4, -1) + inner)
+
+
+def _first_tile_if_periodic(a):
+    """Checks bit for bit that a full-size array repeats the 8^4 pattern and
+    returns the first copy, as (4, 4096, ...)."""
+    inner = a.shape[2:]
+    shp = (4,)
+    for R, T in zip(REPS[::-1], TILE[::-1]):
+        shp += (R, T)
+    b = a.reshape(shp + inner)
+    first = b[:, :1, :, :1, :, :1, :, :1]
+    for mu in range(4):
+        assert (b[mu] == first[mu]).all(), "direction %d breaks the period" % mu
+    return first.reshape((4, -1) + inner)
+
+
+@functools.lru_cache(maxsize=None)
+def _tile_start():
+    """Cooled 8^4 labels, centrifuged, then 12 oracle sweeps of annealed
+    over-improved VP smoothing: the sweeps where rejections set in (337 of
+    16,384 candidates rejected in the next sweep)."""
+    lab = cooled_labels(TILE, 2)
+    U = O.centrifuge(TILE, lab, 0.02, 1234)
+    U, _ = O.smooth(TILE, U, lab, 12, 0.06, eps=-0.25, vp=True)
+    return lab, U
+
+
+def _split_links(Ug, Uo, U0, edge):
+    """Links decided differently (accepted on one side, rejected on the
+    other): the accepted candidate must lie within `edge` rad of a sector edge."""
+    d = np.abs(Ug - Uo).max(axis=(2, 3))
+    split = d > 1e-4
+    for mu, s in zip(*np.nonzero(split)):
+        acc = Ug[mu, s] if np.abs(Ug[mu, s] - U0[mu, s]).max() > 1e-5 else Uo[mu, s]
+        assert _margin(acc) < edge, (mu, s, _margin(acc))
+    return d, split
+
+
+PATHS = [
+    # name, precision, storage, tolerance
+    ("stout", vs.VS_FP32, vs.VS_LINK18, 1e-6),
+    ("stout", vs.VS_FP32, vs.VS_LINK12, 1e-6),
+    ("stout", vs.VS_FP64, vs.VS_LINK18, 1e-12),
+    ("stout_simultaneous", vs.VS_FP32, vs.VS_LINK18, 1e-6),
+    ("aus_maxretr", vs.VS_FP32, vs.VS_LINK18, 1e-6),
+    ("aus_ucp", vs.VS_FP32, vs.VS_LINK18, 3e-6),
+    ("ape_simultaneous", vs.VS_FP32, vs.VS_LINK18, 1.5e-5),
+    ("flow_rk3", vs.VS_FP32, vs.VS_LINK18, 2e-6),
+]
+
+
+@pytest.mark.parametrize("path,prec,storage,tol", PATHS,
+                         ids=["%s-%s-%s" % (p[0], "fp32" if p[1] == vs.VS_FP32 else "fp64",
+                                             "18" if p[2] == vs.VS_LINK18 else "12") for p in PATHS])
+def test_every_link_of_a_periodic_field_at_full_size(path, prec, storage, tol):
+    """One sweep (RK3: one step) of each path on the periodic 32^3 x 64 field,
+    from the same starting field on both sides: the GPU result repeats bit for
+    bit and its first copy matches the oracle's 8^4 sweep link by link, with
+    the same VP decisions except candidates at a sector edge (FP32)."""
+    lab, U0 = _tile_start()
+    ctx = vs.vs_create(0)
+    f = vs.vs_field_create(ctx, FULL, prec, storage)
+    vs.vs_load_field(f, links=_tile(U0))
+    assert np.array_equal(_first_tile_if_periodic(vs.vs_read_labels(f)), lab)
+    eps, rho, alpha = -0.25, 0.06, 0.02
+    if path == "stout":
+        vs.vs_smooth(f, 1, rho, eps, vortex_preserve=True, reunit_every=0)
+        Uo, rej = O.smooth(TILE, U0, lab, 1, rho, eps=eps, vp=True)
+    elif path == "stout_simultaneous":
+        vs.vs_smooth(f, 1, rho, eps, vortex_preserve=True, reunit_every=0, kind=vs.VS_SIMULTANEOUS)
+        Uo, rej = O.smooth(TILE, U0, lab, 1, rho, eps=eps, vp=True, schedule=O.SIMULTANEOUS)
+    elif path == "aus_maxretr":
+        vs.vs_smooth_aus(f, 1, alpha, eps, n_hits=3, reunit_every=0, vortex_preserve=True)
+        Uo, rej = O.aus(TILE, U0, lab, 1, alpha, eps=eps, n_hits=3, vp=True)
+    elif path == "aus_ucp":
+        vs.vs_smooth_ape(f, 1, alpha, eps, reunit_every=0, vortex_preserve=True)
+        Uo, rej = O.ape_ucp(TILE, U0, lab, 1, alpha, eps=eps, vp=True)
+    elif path == "ape_simultaneous":
+        vs.vs_smooth_ape(f, 1, 0.5, eps, schedule=vs.VS_SIMULTANEOUS, reunit_every=0,
+                         vortex_preserve=False)
+        Uo, rej = O.ape_ucp(TILE, U0, None, 1, 0.5, eps=eps, schedule="simultaneous", vp=False)
+    else:
+        vs.vs_flow_rk3(f, 1, 0.02, 1.0, reunit_every=0)
+        Uo, rej = O.flow_rk3(TILE, U0, 1, 0.02, eps=1.0), None
+    assert vs.vs_field_count_nonfinite(f) == 0
+    Ug = _first_tile_if_periodic(vs.vs_read_field(f))
+    vs.vs_field_destroy(f)
+    vs.vs_destroy(ctx)
+
+    d, split = _split_links(Ug, Uo, U0, 1e-5 if prec == vs.VS_FP32 else 1e-10)
+    assert int(split.sum()) <= (8 if prec == vs.VS_FP32 else 0)
+    assert float(d[~split].max()) < tol
+    if rej is not None and path != "ape_simultaneous":
+        assert int(rej.sum()) > 0                  # the sweep exercises rejections
