@@ -107,6 +107,10 @@ MUTATIONS = [
      "r2[k] = conj(r0[a] * r1[b] - r0[b] * r1[a]);",
      "r2[k] = r0[a] * r1[b] - r0[b] * r1[a];",
      pins.test_reunit_rows_are_the_qr_factor_and_special_unitary, ()),
+    ("site index with transposed extents",
+     "return x[0] + (long)g->L[0] * (x[1] + (long)g->L[1] * (x[2] + (long)g->L[2] * x[3]));",
+     "return x[0] + (long)g->L[1] * (x[1] + (long)g->L[0] * (x[2] + (long)g->L[2] * x[3]));",
+     pins.test_periodic_extension_repeats_the_result, ()),
     ("cooling subgroup conjugation",
      "Tc.m[p][q] = -be / k;",
      "Tc.m[p][q] = be / k;",

@@ -1007,3 +1007,37 @@ def test_flow_rk3_invariants():
         W = O.flow_rk3(dims, W, 1, 0.02)
         S.append(O.action(dims, W))
     assert all(s1 < s0 for s0, s1 in zip(S, S[1:]))
+
+
+def test_periodic_extension_repeats_the_result():
+    """Translation covariance of every schedule: the colour classes c_mu(x)
+    repeat with period 4 and every site is treated alike, so a field that
+    repeats an 8^4 field over 16x8x8x16 must give, after a sweep of any path,
+    the 8^4 result repeated, to the bit (the full-size GPU tests rely on this).
+    A neighbour index that wraps with the wrong extent breaks it."""
+    tile, full = (8, 8, 8, 8), (16, 8, 8, 16)
+    reps = tuple(F // T for F, T in zip(full, tile))
+
+    def rep(a):
+        inner = a.shape[2:]
+        t = a.reshape((4,) + tile[::-1] + inner)
+        return np.tile(t, (1,) + reps[::-1] + (1,) * len(inner)).reshape((4, -1) + inner)
+
+    U = O.cool(tile, synth.haar_field(tile, 2), 20)
+    lab = O.labels(tile, U)
+    U = O.centrifuge(tile, lab, 0.02, 1234)
+    U, _ = O.smooth(tile, U, lab, 12, 0.06, eps=-0.25, vp=True)
+    Uf, labf = rep(U), rep(lab)
+    assert np.array_equal(O.labels(full, Uf), labf)
+    paths = [lambda d, u, l: O.smooth(d, u, l, 1, 0.06, eps=-0.25, vp=True),
+             lambda d, u, l: O.smooth(d, u, l, 1, 0.06, eps=-0.25, vp=True, schedule=O.SIMULTANEOUS),
+             lambda d, u, l: O.aus(d, u, l, 1, 0.02, eps=-0.25, vp=True),
+             lambda d, u, l: O.ape_ucp(d, u, l, 1, 0.02, eps=-0.25, vp=True),
+             lambda d, u, l: O.ape_ucp(d, u, None, 1, 0.5, eps=-0.25, schedule="simultaneous", vp=False),
+             lambda d, u, l: (O.flow_rk3(d, u, 1, 0.02, eps=1.0), None)]
+    for run in paths:
+        small, rej_small = run(tile, U, lab)
+        big, rej_big = run(full, Uf, labf)
+        assert np.array_equal(big, rep(small))
+        if rej_small is not None:
+            assert int(rej_big.sum()) == int(rej_small.sum()) * int(np.prod(reps))
