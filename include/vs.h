@@ -118,7 +118,7 @@ vs_status vs_centrifuge(vs_field *f, double omega, uint64_t seed);
 typedef struct {
     int32_t kind;                 /* VS_ANNEALED or VS_SIMULTANEOUS */
     const double *rho_per_sweep;  /* host [n_sweeps] step sizes, or NULL for constant rho */
-    int32_t reunit_every;         /* FP32: re-unitarise (FP64 Gram-Schmidt) every k sweeps; 0 = never */
+    int32_t reunit_every;         /* FP32: re-unitarise (Gram-Schmidt in FP32) every k sweeps; 0 = never */
     int32_t action_every;         /* record <S> in stats every k sweeps; 0 = never */
 } vs_anneal;
 
@@ -290,7 +290,9 @@ vs_status vs_current_labels(vs_field *f, int8_t *labels_out, int32_t where);  /*
  * field is already transformed. */
 vs_status vs_gauge_transform(vs_field *f, const double *G, int32_t where);
 
-/* Re-unitarise every link now (FP64 Gram-Schmidt of rows 1-2, row 3 = conj(r1 x r2)). */
+/* Re-unitarise every link now: Gram-Schmidt of rows 1-2 in the field's precision, row 3 =
+ * conj(r1 x r2); no label test (the periodic pass inside the smoothers keeps a link whose
+ * label would change). */
 vs_status vs_reunitarise(vs_field *f);
 
 /* Wait for all work queued on the field's stream; EDEVICE on a device error. */
