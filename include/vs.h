@@ -86,8 +86,9 @@ void vs_destroy(vs_ctx *ctx);
 
 /* Allocate a field (links + resident reference labels) on the context's
  * device.  stream: a cudaStream_t to run on, or NULL for a library-owned
- * stream.  EINVAL: an extent not a positive multiple of 4, or an unknown
- * precision/storage; EUNSUPPORTED: FP64 with 12-real storage. */
+ * stream.  EINVAL: an extent not a positive multiple of 4, more than 2^30
+ * sites, or an unknown precision/storage; EUNSUPPORTED: FP64 with 12-real
+ * storage. */
 vs_status vs_field_create(vs_ctx *ctx, const int32_t dims[4], int32_t precision,
                           int32_t storage, void *stream, vs_field **out);
 void vs_field_destroy(vs_field *f);

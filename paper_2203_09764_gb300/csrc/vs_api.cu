@@ -104,6 +104,8 @@ static size_t field_bytes(const vs_field *f) {
     return (size_t)4 * f->nc * (size_t)f->g.P * (f->prec == VS_FP64 ? 8 : 4);
 }
 
+// Extents: positive multiples of 4 (the colour classes), at most 2^30 sites so
+// that plane positions and per-site loop indices fit in 32-bit ints.
 static bool valid_dims(const int32_t d[4]) {
     long long v = 1;
     for (int k = 0; k < 4; ++k) {
@@ -125,8 +127,9 @@ extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t p
     if (!c || !dims || !out) return fail(VS_EINVAL, "vs_field_create: NULL argument");
     *out = nullptr;
     if (!valid_dims(dims))
-        return fail(VS_EINVAL, "vs_field_create: extents must be positive multiples of 4 (got %d %d %d %d)",
-                    dims[0], dims[1], dims[2], dims[3]);
+        return fail(VS_EINVAL,
+                    "vs_field_create: extents must be positive multiples of 4 with at most 2^30 sites "
+                    "(got %d %d %d %d)", dims[0], dims[1], dims[2], dims[3]);
     if (precision != VS_FP64 && precision != VS_FP32) return fail(VS_EINVAL, "vs_field_create: bad precision");
     if (storage != VS_LINK18 && storage != VS_LINK12) return fail(VS_EINVAL, "vs_field_create: bad storage");
     if (precision == VS_FP64 && storage == VS_LINK12)
