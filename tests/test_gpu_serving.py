@@ -142,6 +142,33 @@ def test_queue_cap_gives_ebusy():
     vs.vs_destroy(ctx)
 
 
+def test_submit_rejects_bad_jobs():
+    """vs_submit refuses a malformed job before queueing it: extents that are
+    not positive multiples of 4, more than 2^30 sites, a negative count, a
+    centrifuge angle at or above 1/4, a non-finite step, a label outside
+    {-1, 0, 1} (EINVAL); FP64 with 12-real storage (EUNSUPPORTED).  Nothing
+    reaches the queue."""
+    ctx = vs.vs_create(0)
+    dims = (4, 4, 4, 4)
+    bad_labels = np.zeros((4, 256), dtype=np.int8)
+    bad_labels[2, 17] = 2
+    cases = [(vs.make_job((6, 4, 4, 4), 0.05, 1), vs.VS_EINVAL),
+             (vs.make_job((2048, 2048, 2048, 4), 0.05, 1), vs.VS_EINVAL),
+             (vs.make_job(dims, 0.05, -1), vs.VS_EINVAL),
+             (vs.make_job(dims, 0.05, 1, n_cool=-2), vs.VS_EINVAL),
+             (vs.make_job(dims, 0.05, 1, omega=0.25), vs.VS_EINVAL),
+             (vs.make_job(dims, float("nan"), 1), vs.VS_EINVAL),
+             (vs.make_job(dims, 0.05, 1, u0=0.0), vs.VS_EINVAL),
+             (vs.make_job(dims, 0.05, 1, labels=bad_labels), vs.VS_EINVAL),
+             (vs.make_job(dims, 0.05, 1, precision=vs.VS_FP64, storage=vs.VS_LINK12), vs.VS_EUNSUPPORTED)]
+    for job, status in cases:
+        with pytest.raises(vs.VSError) as ei:
+            vs.vs_submit(ctx, job)
+        assert ei.value.status == status
+    assert vs.vs_serve_stats_get(ctx)["submitted"] == 0
+    vs.vs_destroy(ctx)
+
+
 def test_allocation_failure_is_reported_and_isolated():
     """Host-side fault injection: the allocator hook refuses every allocation
     after the first N; the job that hits it reports VS_ENOMEM, memory it did
