@@ -91,6 +91,13 @@ void vs_destroy(vs_ctx *ctx);
  * storage. */
 vs_status vs_field_create(vs_ctx *ctx, const int32_t dims[4], int32_t precision,
                           int32_t storage, void *stream, vs_field **out);
+/* Device memory of a field: the links (4 V x 18 or 12 reals), two label planes
+ * (8 V bytes) and a few KB of counters, allocated here.  One staging buffer is
+ * allocated on first need, grown to the largest need and kept until
+ * vs_field_destroy: host transfers of links or a gauge field (288 V or 144 V
+ * bytes), of labels (4 V) and of per-site observables (24 V), and the second
+ * field buffer of the simultaneous schedules and the RK3 stages (one field's
+ * links).  Device-side transfers (`where` = VS_DEVICE) need no staging. */
 void vs_field_destroy(vs_field *f);
 
 /* Load, Sec. I Eqs. (centre_project)/(centre_element): exactly one of
