@@ -334,6 +334,7 @@ extern "C" vs_status vs_field_restore(vs_field *f, const double *links, const in
 
 extern "C" vs_status vs_read_field(vs_field *f, double *out, int32_t where) {
     if (!f || !out) return fail(VS_EINVAL, "vs_read_field: NULL argument");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_read_field: field not loaded");
     if (where != VS_HOST && where != VS_DEVICE) return fail(VS_EINVAL, "vs_read_field: bad `where`");
     CK(cudaSetDevice(f->ctx->opt.device));
     const size_t bytes = 4 * (size_t)f->g.V * 18 * sizeof(double);
@@ -351,6 +352,7 @@ extern "C" vs_status vs_read_field(vs_field *f, double *out, int32_t where) {
 
 static vs_status read_labels_impl(vs_field *f, int8_t *out, int32_t where, bool current) {
     if (!f || !out) return fail(VS_EINVAL, "read labels: NULL argument");
+    if (!f->loaded) return fail(VS_EINVAL, "read labels: field not loaded");
     if (where != VS_HOST && where != VS_DEVICE) return fail(VS_EINVAL, "read labels: bad `where`");
     CK(cudaSetDevice(f->ctx->opt.device));
     const size_t n = 4 * (size_t)f->g.V;
@@ -456,6 +458,7 @@ extern "C" vs_status vs_gauge_transform(vs_field *f, const double *G, int32_t wh
 
 extern "C" vs_status vs_reunitarise(vs_field *f) {
     if (!f) return fail(VS_EINVAL, "vs_reunitarise: NULL field");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_reunitarise: field not loaded");
     CK(cudaSetDevice(f->ctx->opt.device));
     CK(launch_reunit(f->prec == VS_FP32, f->nc, f->g, f->U, nullptr, f->stream));
     return VS_OK;
@@ -503,6 +506,7 @@ static SubsweepParams make_params(vs_field *f, double rho, double eps, double u0
 extern "C" vs_status vs_subsweep(vs_field *f, int32_t mu, int32_t colour, double rho, double eps, double u0,
                                  int32_t vp) {
     if (!f) return fail(VS_EINVAL, "vs_subsweep: NULL field");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_subsweep: field not loaded");
     if (mu < 0 || mu > 3 || colour < 0 || colour > 3) return fail(VS_EINVAL, "vs_subsweep: bad mu/colour");
     vs_status st = check_smooth_params(rho, eps, u0);
     if (st) return st;
@@ -901,6 +905,7 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
 
 extern "C" vs_status vs_action(vs_field *f, double *mean_S) {
     if (!f || !mean_S) return fail(VS_EINVAL, "vs_action: NULL argument");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_action: field not loaded");
     CK(cudaSetDevice(f->ctx->opt.device));
     CK(launch_action(f->prec == VS_FP32, f->nc, f->g, f->U, f->partials, f->d_result, f->stream));
     CK(cudaMemcpyAsync(mean_S, f->d_result, sizeof(double), cudaMemcpyDeviceToHost, f->stream));
@@ -911,6 +916,7 @@ extern "C" vs_status vs_action(vs_field *f, double *mean_S) {
 extern "C" vs_status vs_observables(vs_field *f, vs_observables_out *out, double *S_site, double *SR_site,
                                     double *q_site, int32_t where) {
     if (!f || !out) return fail(VS_EINVAL, "vs_observables: NULL argument");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_observables: field not loaded");
     if (where != VS_HOST && where != VS_DEVICE) return fail(VS_EINVAL, "vs_observables: bad `where`");
     CK(cudaSetDevice(f->ctx->opt.device));
     const size_t V = f->g.V;
@@ -942,6 +948,7 @@ extern "C" vs_status vs_observables(vs_field *f, vs_observables_out *out, double
 
 extern "C" vs_status vs_vortex_check(vs_field *f, vs_vortex_report *out) {
     if (!f || !out) return fail(VS_EINVAL, "vs_vortex_check: NULL argument");
+    if (!f->loaded) return fail(VS_EINVAL, "vs_vortex_check: field not loaded");
     CK(cudaSetDevice(f->ctx->opt.device));
     unsigned long long *cnt = f->d_counts + 2;      // [3] counts, [1] margin bits
     CK(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), f->stream));

@@ -441,6 +441,30 @@ def test_zero_sweeps_and_bad_extents(ctx):
         assert ei.value.status == vs.VS_EINVAL
 
 
+def test_calls_on_a_field_never_loaded_are_refused(ctx):
+    """A created field holds uninitialised device memory until a load: every
+    call that reads the links or the labels refuses it with VS_EINVAL rather
+    than returning garbage, and the field still works after a load."""
+    dims = (4, 4, 4, 8)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    calls = [lambda: vs.vs_read_field(f), lambda: vs.vs_read_labels(f), lambda: vs.vs_current_labels(f),
+             lambda: vs.vs_reunitarise(f), lambda: vs.vs_subsweep(f, 0, 0, 0.05, -0.25),
+             lambda: vs.vs_action(f), lambda: vs.vs_observables(f), lambda: vs.vs_vortex_check(f),
+             lambda: vs.vs_field_count_nonfinite(f), lambda: vs.vs_centrifuge(f, 0.02, 1),
+             lambda: vs.vs_smooth(f, 1, 0.05, -0.25), lambda: vs.vs_smooth_aus(f, 1, 0.02),
+             lambda: vs.vs_smooth_ape(f, 1, 0.02), lambda: vs.vs_flow_rk3(f, 1, 0.02),
+             lambda: vs.vs_field_checkpoint(f)]
+    for call in calls:
+        with pytest.raises(vs.VSError) as ei:
+            call()
+        assert ei.value.status == vs.VS_EINVAL
+    lab = synth.iid_labels(dims, 3)
+    vs.vs_load_field(f, labels=lab)
+    assert np.array_equal(vs.vs_read_labels(f), lab)
+    assert vs.vs_vortex_check(f)["n_label_diff"] == 0
+    vs.vs_field_destroy(f)
+
+
 def test_fp32_vp_200_free_running_sweeps_keep_vortex_structure(ctx):
     """200 free-running FP32 sweeps with VP: every label and centre charge
     equals the original (and the FP64 oracle's), and the mean action, a
