@@ -24,6 +24,9 @@
  *   The caller keeps ownership of every buffer it passes in; the library
  *     copies what it needs before the call returns (host) or before work on
  *     the field's stream that follows the call (device).
+ *   A field holds no data until vs_load_field, vs_load_cooled or
+ *     vs_field_restore: every other call that reads or updates its links or
+ *     labels returns EINVAL before that.
  *   Every call returns a vs_status; on failure vs_last_error() describes it.
  *     No C++ exception crosses this boundary.  Calls on one vs_field are not
  *     thread safe; distinct fields may be used from distinct threads.
