@@ -123,7 +123,8 @@ vs_status vs_load_cooled(vs_field *f, uint64_t seed, int32_t n_cool);
  * per link from SplitMix64 value (mu*V + s) of `seed` mod 3 selecting
  * (1,2),(2,3),(3,1); lambda^j = lambda + delta, lambda^k = lambda - delta,
  * delta = omega (sigma - lambda).  EINVAL unless 0 <= omega < 1/4 (the bound
- * that keeps every label, Sec. IV.A). */
+ * that keeps every label, Sec. IV.A), or if the field is in a random gauge
+ * (vs_gauge_transform comes after the centrifuge). */
 vs_status vs_centrifuge(vs_field *f, double omega, uint64_t seed);
 
 typedef struct {

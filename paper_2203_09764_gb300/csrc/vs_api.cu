@@ -388,6 +388,8 @@ extern "C" vs_status vs_centrifuge(vs_field *f, double omega, uint64_t seed) {
     if (!(omega >= 0.0 && omega < 0.25))
         return fail(VS_EINVAL, "vs_centrifuge: omega = %g outside [0, 1/4)", omega);
     if (!f->loaded) return fail(VS_EINVAL, "vs_centrifuge: field not loaded");
+    // the centrifuged links are built in the original gauge from the labels
+    if (f->gauge_on) return fail(VS_EINVAL, "vs_centrifuge: field in a random gauge (centrifuge first)");
     CK(cudaSetDevice(f->ctx->opt.device));
     CK(launch_centrifuge(f->prec == VS_FP32, f->nc, f->g, f->ref, omega, seed, f->U, f->stream));
     return VS_OK;

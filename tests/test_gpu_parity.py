@@ -172,14 +172,26 @@ def test_nonfinite_links_are_counted(ctx, prec, storage):
     vs.vs_field_destroy(f)
 
 
-def test_checkpoint_refuses_gauge_transformed_fields(ctx):
+def test_checkpoint_and_centrifuge_refuse_gauge_transformed_fields(ctx):
+    """A field in a random gauge keeps G on the device: a checkpoint would
+    lose it (EUNSUPPORTED), and the centrifuge, which builds links from the
+    labels in the original gauge, would leave links and G inconsistent
+    (EINVAL).  A second transform is refused too; a reload drops G."""
     dims = (4, 4, 4, 4)
     f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
-    vs.vs_load_field(f, labels=synth.iid_labels(dims, 3))
+    lab = synth.iid_labels(dims, 3)
+    vs.vs_load_field(f, labels=lab)
     vs.vs_gauge_transform(f, synth.random_gauge(dims, 4))
     with pytest.raises(vs.VSError) as ei:
         vs.vs_field_checkpoint(f)
     assert ei.value.status == vs.VS_EUNSUPPORTED
+    for call in (lambda: vs.vs_centrifuge(f, 0.02, 1), lambda: vs.vs_gauge_transform(f, synth.random_gauge(dims, 5))):
+        with pytest.raises(vs.VSError) as ei:
+            call()
+        assert ei.value.status == vs.VS_EINVAL
+    vs.vs_load_field(f, labels=lab)
+    vs.vs_centrifuge(f, 0.02, 1)
+    assert vs.vs_vortex_check(f)["n_label_diff"] == 0
     vs.vs_field_destroy(f)
 
 
