@@ -323,7 +323,7 @@ typedef struct {
     int64_t n_sites;
     int64_t plane_stride;          /* P: sites per vector plane */
     int32_t n_components;          /* NC: 18 or 12 stored reals per link */
-    int32_t pad;
+    int32_t device;                /* CUDA device ordinal that holds the field */
     void *links;                   /* device: direction mu at element mu*NC*P, split into
                                       vector planes: FP32 18 reals = 4 float4 planes
                                       (complex entries 0-1, 2-3, 4-5, 6-7) + 1 float2 plane

@@ -203,6 +203,7 @@ extern "C" vs_status vs_field_describe(const vs_field *f, vs_field_desc *d) {
     d->n_sites = f->g.V;
     d->plane_stride = f->g.P;
     d->n_components = f->nc;
+    d->device = f->ctx->opt.device;
     d->links = f->U;
     d->labels = f->ref;
     d->stream = (void *)f->stream;

@@ -67,7 +67,7 @@ class vs_field_desc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 4), ("precision", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("n_sites", ctypes.c_int64),
                 ("plane_stride", ctypes.c_int64), ("n_components", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("links", ctypes.c_void_p),
+                ("device", ctypes.c_int32), ("links", ctypes.c_void_p),
                 ("labels", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
 
 
@@ -182,6 +182,43 @@ def _ptr(a):
     raise TypeError("expected a numpy array or a torch tensor")
 
 
+def _host_links(a):
+    """Host link or gauge input: complex128 as it is, float64 as (re, im)
+    pairs, any other numeric type converted to complex128."""
+    if a.dtype == np.float64:
+        return np.ascontiguousarray(a)
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _buf(f, a, kind, n_entries, what):
+    """(pointer, where) of a buffer the library reads or writes for field f,
+    after checking what the C side cannot: the element type (kind "c" for
+    complex128 entries, given as complex128 or as float64 (re, im) pairs, "i8"
+    for labels), contiguity, the byte size (n_entries of 16 or 1 bytes), and
+    for a CUDA tensor the field's device."""
+    nbytes = n_entries * (16 if kind == "c" else 1)
+    if isinstance(a, np.ndarray):
+        ok = a.dtype in (np.complex128, np.float64) if kind == "c" else a.dtype == np.int8
+        size, contiguous = a.nbytes, a.flags["C_CONTIGUOUS"]
+    elif hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+        ok = a.dtype in (torch.complex128, torch.float64) if kind == "c" else a.dtype == torch.int8
+        size, contiguous = a.numel() * a.element_size(), a.is_contiguous()
+        if a.is_cuda and a.device.index != vs_field_describe(f)["device"]:
+            raise ValueError("%s: tensor on %s, the field is on cuda:%d"
+                             % (what, a.device, vs_field_describe(f)["device"]))
+    else:
+        raise TypeError("%s: expected a numpy array or a torch tensor" % what)
+    if not ok:
+        raise TypeError("%s: element type %s (expected %s)"
+                        % (what, a.dtype, "complex128 or float64 pairs" if kind == "c" else "int8"))
+    if not contiguous:
+        raise ValueError("%s: buffer must be contiguous" % what)
+    if size != nbytes:
+        raise ValueError("%s: buffer of %d bytes, the field needs %d" % (what, size, nbytes))
+    return _ptr(a)
+
+
 def _dims(dims):
     return (ctypes.c_int32 * 4)(*[int(d) for d in dims])
 
@@ -271,15 +308,16 @@ def vs_field_destroy(f):
 def vs_load_field(f, links=None, labels=None):
     if (links is None) == (labels is None):
         raise ValueError("give exactly one of links / labels")
+    V = _field_sites(f)
     if links is not None:
         if isinstance(links, np.ndarray):
-            links = np.ascontiguousarray(links, dtype=np.complex128)
-        p, where = _ptr(links)
+            links = _host_links(links)
+        p, where = _buf(f, links, "c", 36 * V, "vs_load_field links")
         _check(lib.vs_load_field(f, p, None, where))
     else:
         if isinstance(labels, np.ndarray):
             labels = np.ascontiguousarray(labels, dtype=np.int8)
-        p, where = _ptr(labels)
+        p, where = _buf(f, labels, "i8", 4 * V, "vs_load_field labels")
         _check(lib.vs_load_field(f, None, p, where))
 
 
@@ -408,10 +446,10 @@ def _field_sites(f):
 
 def vs_read_field(f, out=None):
     """Current links as complex128 [4][V][3][3] (host), or into `out` (numpy or torch CUDA)."""
+    V = _field_sites(f)
     if out is None:
-        V = _field_sites(f)
         out = np.empty((4, V, 3, 3), dtype=np.complex128)
-    p, where = _ptr(out)
+    p, where = _buf(f, out, "c", 36 * V, "vs_read_field out")
     _check(lib.vs_read_field(f, p, where))
     return out
 
@@ -431,8 +469,8 @@ def vs_field_checkpoint(f, links_out=None, labels_out=None):
         links_out = np.empty((4, V, 3, 3), dtype=np.complex128)
     if labels_out is None:
         labels_out = np.empty((4, V), dtype=np.int8)
-    pl, where = _ptr(links_out)
-    pn, where2 = _ptr(labels_out)
+    pl, where = _buf(f, links_out, "c", 36 * V, "vs_field_checkpoint links_out")
+    pn, where2 = _buf(f, labels_out, "i8", 4 * V, "vs_field_checkpoint labels_out")
     if where != where2:
         raise ValueError("links_out and labels_out must both be host or both device buffers")
     n = ctypes.c_int64(0)
@@ -443,29 +481,32 @@ def vs_field_checkpoint(f, links_out=None, labels_out=None):
 def vs_field_restore(f, links, labels, sweeps_done):
     """Load a checkpoint (as vs_field_checkpoint returns it) into a field of the
     same dims, precision and storage."""
+    V = _field_sites(f)
     if isinstance(links, np.ndarray):
-        links = np.ascontiguousarray(links, dtype=np.complex128)
+        links = _host_links(links)
     if isinstance(labels, np.ndarray):
         labels = np.ascontiguousarray(labels, dtype=np.int8)
-    pl, where = _ptr(links)
-    pn, where2 = _ptr(labels)
+    pl, where = _buf(f, links, "c", 36 * V, "vs_field_restore links")
+    pn, where2 = _buf(f, labels, "i8", 4 * V, "vs_field_restore labels")
     if where != where2:
         raise ValueError("links and labels must both be host or both device buffers")
     _check(lib.vs_field_restore(f, pl, pn, int(sweeps_done), where))
 
 
 def vs_read_labels(f, out=None):
+    V = _field_sites(f)
     if out is None:
-        out = np.empty((4, _field_sites(f)), dtype=np.int8)
-    p, where = _ptr(out)
+        out = np.empty((4, V), dtype=np.int8)
+    p, where = _buf(f, out, "i8", 4 * V, "vs_read_labels out")
     _check(lib.vs_read_labels(f, p, where))
     return out
 
 
 def vs_current_labels(f, out=None):
+    V = _field_sites(f)
     if out is None:
-        out = np.empty((4, _field_sites(f)), dtype=np.int8)
-    p, where = _ptr(out)
+        out = np.empty((4, V), dtype=np.int8)
+    p, where = _buf(f, out, "i8", 4 * V, "vs_current_labels out")
     _check(lib.vs_current_labels(f, p, where))
     return out
 
@@ -473,8 +514,8 @@ def vs_current_labels(f, out=None):
 def vs_gauge_transform(f, G):
     """Apply the random gauge transformation G (complex [V][3][3], numpy or torch CUDA)."""
     if isinstance(G, np.ndarray):
-        G = np.ascontiguousarray(G, dtype=np.complex128)
-    p, where = _ptr(G)
+        G = _host_links(G)
+    p, where = _buf(f, G, "c", 9 * _field_sites(f), "vs_gauge_transform G")
     _check(lib.vs_gauge_transform(f, p, where))
 
 
@@ -501,8 +542,8 @@ def vs_field_describe(f):
     d = vs_field_desc()
     _check(lib.vs_field_describe(f, ctypes.byref(d)))
     return dict(dims=tuple(d.dims), precision=d.precision, storage=d.storage, n_sites=d.n_sites,
-                plane_stride=d.plane_stride, n_components=d.n_components, links=d.links,
-                labels=d.labels, stream=d.stream)
+                plane_stride=d.plane_stride, n_components=d.n_components, device=d.device,
+                links=d.links, labels=d.labels, stream=d.stream)
 
 
 def vs_layout_index(dims, x):

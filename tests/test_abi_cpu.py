@@ -68,3 +68,37 @@ def test_oracle_is_not_imported_by_the_product():
                     txt = f.read()
                 assert "import oracle" not in txt and "from oracle" not in txt, fn
                 assert "vs_oracle" not in txt, fn
+
+
+def test_binding_checks_buffers_before_the_call(libvs):
+    """The binding checks what the C side cannot see in a plain pointer: the
+    element type, contiguity and byte size of every buffer (host arrays here;
+    CUDA tensors also get a device check), so a wrong buffer raises in Python
+    instead of reaching a kernel."""
+    import numpy as np
+    import torch
+    from paper_2203_09764_gb300 import vs
+    V = 16
+    ok = [(np.zeros((4, V, 3, 3), np.complex128), "c", 36 * V),
+          (np.zeros((4, V, 3, 3, 2), np.float64), "c", 36 * V),
+          (torch.zeros((4, V, 3, 3), dtype=torch.complex128), "c", 36 * V),
+          (np.zeros((4, V), np.int8), "i8", 4 * V),
+          (torch.zeros((4, V), dtype=torch.int8), "i8", 4 * V)]
+    for a, kind, n in ok:
+        p, where = vs._buf(None, a, kind, n, "buffer")
+        assert where == vs.VS_HOST and p.value
+    bad = [(np.zeros((4, V, 3, 3), np.complex64), "c", 36 * V, TypeError),
+           (torch.zeros((4, V, 3, 3), dtype=torch.complex64), "c", 36 * V, TypeError),
+           (np.zeros((4, V, 3, 3), np.float64), "c", 36 * V, ValueError),        # real, half the bytes
+           (np.zeros((4, V - 1, 3, 3), np.complex128), "c", 36 * V, ValueError),
+           (np.zeros((4, 2 * V, 3, 3), np.complex128)[:, ::2], "c", 36 * V, ValueError),
+           (np.zeros((4, V), np.int16), "i8", 4 * V, TypeError),
+           (np.zeros((4, V + 1), np.int8), "i8", 4 * V, ValueError),
+           ([0] * (4 * V), "i8", 4 * V, TypeError)]
+    for a, kind, n, err in bad:
+        with pytest.raises(err):
+            vs._buf(None, a, kind, n, "buffer")
+    # host link input: complex128 and float64 pairs pass unchanged, others convert
+    a = np.zeros((4, V, 3, 3, 2))
+    assert vs._host_links(a) is a
+    assert vs._host_links(np.zeros((4, V, 3, 3), np.complex64)).dtype == np.complex128

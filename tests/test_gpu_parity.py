@@ -477,6 +477,28 @@ def test_calls_on_a_field_never_loaded_are_refused(ctx):
     vs.vs_field_destroy(f)
 
 
+def test_binding_checks_cuda_buffers(ctx):
+    """CUDA tensors handed to the binding are checked for element type, size
+    and device before the library sees the pointer; a correct one round-trips."""
+    torch = pytest.importorskip("torch")
+    dims = (4, 4, 4, 8)
+    V = int(np.prod(dims))
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=synth.iid_labels(dims, 5))
+    assert vs.vs_field_describe(f)["device"] == 0
+    with pytest.raises(TypeError):
+        vs.vs_read_field(f, torch.empty((4, V, 3, 3), dtype=torch.complex64, device="cuda:0"))
+    with pytest.raises(ValueError):
+        vs.vs_read_labels(f, torch.empty((4, V - 1), dtype=torch.int8, device="cuda:0"))
+    with pytest.raises(ValueError):
+        vs.vs_load_field(f, links=torch.empty((4, V, 3, 3), dtype=torch.complex128, device="cuda:0")[:, :, :2])
+    out = torch.empty((4, V, 3, 3), dtype=torch.complex128, device="cuda:0")
+    vs.vs_read_field(f, out)
+    vs.vs_synchronize(f)
+    assert np.array_equal(out.cpu().numpy(), vs.vs_read_field(f))
+    vs.vs_field_destroy(f)
+
+
 def test_fp32_vp_200_free_running_sweeps_keep_vortex_structure(ctx):
     """200 free-running FP32 sweeps with VP: every label and centre charge
     equals the original (and the FP64 oracle's), and the mean action, a
