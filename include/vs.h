@@ -240,23 +240,28 @@ vs_status vs_vortex_check(vs_field *f, vs_vortex_report *out);
 /* Vortex check that allocates nothing.  The paper has no counterpart: this
  * is a service for callers that cannot allocate device memory at the point
  * where they need the check -- code running while a CUDA graph is being
- * captured, a serving loop under a hard memory cap that must not call into
- * cudaMalloc (which can block on the whole device or fail under pressure),
- * or a host that hands the library preallocated buffers and forbids any
- * other allocation.  It runs the same kernels as vs_vortex_check on buffers
- * the caller owns: links and ref_labels are device pointers in the layout of
- * a field with these dims, precision and storage (vs_field_describe gives
- * them); the result goes to the caller's host struct.  Its scratch (one byte
- * per link plus eight counters) is a fixed array of VS_NOALLOC_MAX_LINKS
- * bytes compiled into the library, which every GPU that loads the library
- * keeps until the process exits.  EINVAL for lattices with more than
- * VS_NOALLOC_MAX_LINKS links (2,097,152 sites, e.g. 32^3 x 64).  Runs on the
- * calling thread's current device, which must own the buffers; the first
- * call on a device looks up the scratch address there, so make that first
- * call before any stream capture.  All calls share the one scratch array
- * (it keeps the last call's contents; the counters are cleared each call):
- * calls whose work overlaps on the GPU, e.g. on two streams at once, race.
- * Synchronous on `stream` (NULL: the legacy default stream). */
+ * captured on another stream of the thread (the global capture mode forbids
+ * allocating and synchronising calls), a serving loop under a hard memory cap
+ * that must not call into cudaMalloc (which can block on the whole device or
+ * fail under pressure), or a host that hands the library preallocated buffers
+ * and forbids any other allocation.  It runs the same kernels as
+ * vs_vortex_check on buffers the caller owns: links and ref_labels are device
+ * pointers in the layout of a field with these dims, precision and storage
+ * (vs_field_describe gives them); the result goes to the caller's host struct.
+ * Its scratch (one byte per link plus eight counters) is a fixed array of
+ * VS_NOALLOC_MAX_LINKS bytes compiled into the library, which every GPU that
+ * loads the library keeps until the process exits.  EINVAL for lattices with
+ * more than VS_NOALLOC_MAX_LINKS links (2,097,152 sites, e.g. 32^3 x 64).  Runs
+ * on the calling thread's current device, which must own the buffers.  The
+ * first call on a device looks up the scratch there and pins a 64-byte mapped
+ * host block, so make that first call before any capture.  The call waits for
+ * its own work without a synchronising CUDA call: its last kernel writes the
+ * report and a sequence number to the mapped block, which the host watches
+ * (EDEVICE after 30 s without it).  Calls on one device are serialised, so
+ * they never share the scratch on the GPU.  `stream`: where the kernels run;
+ * while another stream captures, give a non-blocking stream (work on the
+ * legacy default stream, NULL, synchronises with the blocking streams, which
+ * a capture forbids). */
 #define VS_NOALLOC_MAX_LINKS (8 * 1024 * 1024)
 vs_status vs_vortex_check_noalloc(const void *links, const int8_t *ref_labels, const int32_t dims[4],
                                   int32_t precision, int32_t storage, void *stream,

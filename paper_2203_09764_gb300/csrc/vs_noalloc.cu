@@ -4,9 +4,16 @@
 // counters), which a field allocates when it is created.  This entry point
 // runs the same two kernels on buffers the caller already owns and keeps the
 // scratch in a fixed, file-scope device array instead, so it never calls
-// cudaMalloc, cudaFree or an allocating library routine.
+// cudaMalloc, cudaFree or an allocating library routine.  It also makes no
+// synchronising CUDA call, so it stays usable while another stream of the
+// thread captures a graph in the global capture mode: a last one-thread
+// kernel publishes the counters and a sequence number into a small mapped
+// host block, and the host waits for that number (with a time limit).
+#include <atomic>
+#include <chrono>
 #include <cstring>
 #include <mutex>
+#include <thread>
 
 #include "vs_api_internal.h"
 
@@ -18,35 +25,56 @@ using namespace vs;
 static __device__ __align__(256) int8_t g_noalloc_labels[VS_NOALLOC_MAX_LINKS];
 static __device__ __align__(256) unsigned long long g_noalloc_counts[8];
 
+// Copy the four report words to the mapped host block, then the sequence
+// number: the host reads the words once it sees the number.
+__global__ void k_noalloc_publish(const unsigned long long *cnt, volatile unsigned long long *host,
+                                  unsigned long long seq) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) host[k] = cnt[k];
+        __threadfence_system();
+        host[4] = seq;
+    }
+}
+
 namespace {
 
 constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-int8_t *g_labels_addr[kMaxDevices];
-unsigned long long *g_counts_addr[kMaxDevices];
-bool g_ready[kMaxDevices];
+constexpr double kWaitLimitMs = 30000.0;   // the check takes milliseconds; a GPU that stalls this long is lost
 
-// Device addresses of the scratch arrays on the current device, looked up once
-// per device (host code cannot use the arrays' names as device pointers).
-vs_status scratch_of_current_device(int8_t **labels, unsigned long long **counts) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices)
-        return fail(VS_EUNSUPPORTED, "vs_vortex_check_noalloc: device %d beyond %d", dev, kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_ready[dev]) {
-        void *pl = nullptr, *pc = nullptr;
-        e = cudaGetSymbolAddress(&pl, g_noalloc_labels);
-        if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetSymbolAddress(labels)");
-        e = cudaGetSymbolAddress(&pc, g_noalloc_counts);
-        if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetSymbolAddress(counters)");
-        g_labels_addr[dev] = static_cast<int8_t *>(pl);
-        g_counts_addr[dev] = static_cast<unsigned long long *>(pc);
-        g_ready[dev] = true;
+struct DeviceScratch {
+    std::mutex mu;                          // one call at a time per device: the scratch is shared
+    bool ready = false;
+    int8_t *labels = nullptr;
+    unsigned long long *counts = nullptr;
+    volatile unsigned long long *host = nullptr;   // mapped pinned block: 4 report words + sequence
+    unsigned long long *host_dev = nullptr;        // its device address
+    unsigned long long seq = 0;
+};
+DeviceScratch g_dev[kMaxDevices];
+
+// First call on a device: the device addresses of the scratch arrays (host
+// code cannot use the arrays' names as device pointers) and the mapped host
+// block.  Called with the device's mutex held.
+vs_status setup(DeviceScratch &d) {
+    if (d.ready) return VS_OK;
+    void *pl = nullptr, *pc = nullptr, *ph = nullptr, *phd = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&pl, g_noalloc_labels);
+    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetSymbolAddress(labels)");
+    e = cudaGetSymbolAddress(&pc, g_noalloc_counts);
+    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetSymbolAddress(counters)");
+    e = cudaHostAlloc(&ph, 8 * sizeof(unsigned long long), cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaHostAlloc");
+    e = cudaHostGetDevicePointer(&phd, ph, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(ph);
+        return cuda_fail(e, "vs_vortex_check_noalloc: cudaHostGetDevicePointer");
     }
-    *labels = g_labels_addr[dev];
-    *counts = g_counts_addr[dev];
+    memset(ph, 0, 8 * sizeof(unsigned long long));
+    d.labels = static_cast<int8_t *>(pl);
+    d.counts = static_cast<unsigned long long *>(pc);
+    d.host = static_cast<volatile unsigned long long *>(ph);
+    d.host_dev = static_cast<unsigned long long *>(phd);
+    d.ready = true;
     return VS_OK;
 }
 
@@ -74,9 +102,14 @@ extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *re
                     "vs_vortex_check_noalloc: %lld links exceed the fixed scratch of %lld links "
                     "(at most %lld sites); use vs_vortex_check for larger lattices",
                     4 * V, (long long)VS_NOALLOC_MAX_LINKS, (long long)VS_NOALLOC_MAX_LINKS / 4);
-    int8_t *cur = nullptr;
-    unsigned long long *cnt = nullptr;
-    vs_status st = scratch_of_current_device(&cur, &cnt);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(VS_EUNSUPPORTED, "vs_vortex_check_noalloc: device %d beyond %d", dev, kMaxDevices);
+    DeviceScratch &d = g_dev[dev];
+    std::lock_guard<std::mutex> lock(d.mu);
+    vs_status st = setup(d);
     if (st) return st;
     Geo g;
     for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
@@ -84,17 +117,32 @@ extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *re
     g.V = (int)V;
     g.P = V;
     cudaStream_t s = (cudaStream_t)stream;
+    const unsigned long long seq = ++d.seq;
     // counters start at zero, the minimum margin at a huge value; the label
     // plane needs no clearing (every link's entry is written before it is read)
-    cudaError_t e = cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s);
+    unsigned long long *cnt = d.counts;
+    e = cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt + 3, 0x7f, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-        e = launch_vortex(precision == VS_FP32, storage == VS_LINK12 ? 12 : 18, g, links, ref_labels, cur,
+        e = launch_vortex(precision == VS_FP32, storage == VS_LINK12 ? 12 : 18, g, links, ref_labels, d.labels,
                           cnt, cnt + 3, s);
-    unsigned long long h[4] = {0, 0, 0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        k_noalloc_publish<<<1, 32, 0, s>>>(cnt, d.host_dev, seq);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc");
+    // wait for the sequence number: spin briefly, then sleep between looks
+    const auto t0 = std::chrono::steady_clock::now();
+    for (long n = 0; d.host[4] != seq; ++n) {
+        if (n > 1000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if ((n & 255) == 0 &&
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > kWaitLimitMs)
+            return fail(VS_EDEVICE, "vs_vortex_check_noalloc: no result from the GPU after %.0f ms", kWaitLimitMs);
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    unsigned long long h[4];
+    for (int k = 0; k < 4; ++k) h[k] = d.host[k];
     out->n_links = 4 * V;
     out->n_label_diff = (int64_t)h[0];
     out->n_charge_diff = (int64_t)h[1];

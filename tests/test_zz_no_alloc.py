@@ -57,3 +57,34 @@ def test_noalloc_rejects_lattices_beyond_its_scratch():
     assert ei.value.status == vs.VS_EINVAL
     assert "scratch" in str(ei.value)
     assert 4 * 32 * 32 * 32 * 64 <= vs.VS_NOALLOC_MAX_LINKS
+
+
+def test_noalloc_while_another_stream_captures_a_graph():
+    """The use the call exists for: a graph is being captured on another
+    stream of this thread (torch's default global capture mode, which forbids
+    allocation), and the check runs on the field's own stream in the middle
+    of it.  The report equals vs_vortex_check's and the captured graph still
+    replays correctly."""
+    torch = pytest.importorskip("torch")
+    dims = (8, 8, 8, 16)
+    ctx = vs.vs_create(0)
+    try:
+        f = _smoothed_field(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+        ref = vs.vs_vortex_check(f)
+        d = vs.vs_field_describe(f)
+        args = (d["links"], d["labels"], dims, vs.VS_FP32, vs.VS_LINK18, d["stream"])
+        vs.vs_vortex_check_noalloc(*args)            # first call on this device: before any capture
+        x = torch.zeros(4096, device="cuda:0")
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            x.add_(1.0)
+            got = vs.vs_vortex_check_noalloc(*args)
+            x.mul_(3.0)
+        g.replay()
+        torch.cuda.synchronize()
+        vs.vs_field_destroy(f)
+    finally:
+        vs.vs_destroy(ctx)
+    assert got == ref
+    assert float(x[0]) == 3.0 and float(x[-1]) == 3.0
