@@ -499,6 +499,48 @@ def test_binding_checks_cuda_buffers(ctx):
     vs.vs_field_destroy(f)
 
 
+def test_device_buffers_round_trip(ctx):
+    """The device side of the ABI (where = VS_DEVICE, torch CUDA tensors):
+    labels loaded from the device, a checkpoint written to device buffers
+    and restored from them resumes bit for bit, and a gauge field given on
+    the device acts as the same field given on the host."""
+    torch = pytest.importorskip("torch")
+    dims = (4, 8, 4, 8)
+    V = int(np.prod(dims))
+    lab = synth.iid_labels(dims, 9)
+    lab_d = torch.from_numpy(lab).to("cuda:0")
+    G = synth.random_gauge(dims, 11)
+    G_d = torch.from_numpy(G).to("cuda:0")
+    torch.cuda.synchronize()                      # the library's streams do not wait for torch's
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=lab_d)
+    assert np.array_equal(vs.vs_read_labels(f), lab)
+    vs.vs_centrifuge(f, 0.02, 7)
+    vs.vs_smooth(f, 3, 0.06, -0.25, reunit_every=2)
+    L = torch.empty((4, V, 3, 3), dtype=torch.complex128, device="cuda:0")
+    N = torch.empty((4, V), dtype=torch.int8, device="cuda:0")
+    _, _, n = vs.vs_field_checkpoint(f, L, N)
+    vs.vs_synchronize(f)
+    assert n == 3
+    assert np.array_equal(L.cpu().numpy(), vs.vs_read_field(f))
+    assert np.array_equal(N.cpu().numpy(), lab)
+    g = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    vs.vs_field_restore(g, L, N, n)
+    vs.vs_smooth(f, 3, 0.06, -0.25, reunit_every=2)
+    vs.vs_smooth(g, 3, 0.06, -0.25, reunit_every=2)
+    assert np.array_equal(vs.vs_read_field(f), vs.vs_read_field(g))
+    vs.vs_field_destroy(g)
+    vs.vs_field_destroy(f)
+    a = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    b = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    for h, gauge in ((a, G_d), (b, G)):
+        vs.vs_load_field(h, labels=lab)
+        vs.vs_gauge_transform(h, gauge)
+    assert np.array_equal(vs.vs_read_field(a), vs.vs_read_field(b))
+    vs.vs_field_destroy(a)
+    vs.vs_field_destroy(b)
+
+
 def test_fp32_vp_200_free_running_sweeps_keep_vortex_structure(ctx):
     """200 free-running FP32 sweeps with VP: every label and centre charge
     equals the original (and the FP64 oracle's), and the mean action, a
