@@ -189,6 +189,34 @@ def test_generator_is_action_gradient_finite_difference(eps):
         assert abs(np.trace(Q)) < 1e-13                       # traceless
 
 
+def test_generator_is_action_gradient_on_every_link_of_a_2x2x2x2_lattice():
+    """Brute force on the smallest periodic lattice, 2^4: every +-2 shift
+    wraps onto the site itself, so a tall rectangle of a link runs through
+    that same link backwards and the staple sum must count each occurrence.
+    The generator of every one of the 64 links equals the central-difference
+    gradient of the action W (Sec. II.B, Eq. over-improvement) to 2e-6."""
+    dims = (2, 2, 2, 2)
+    U = synth.haar_field(dims, seed=37)
+    c0, c1 = O.overimproved_coeffs(-0.25)
+    T = L.gell_mann_generators()
+    h = 1e-4
+    worst = 0.0
+    for mu in range(4):
+        for s in range(16):
+            x = (s % 2, (s // 2) % 2, (s // 4) % 2, s // 8)
+            Q = O.stout_generator(O.staple_sum(dims, U, mu, x, c0, c1) @ L.dag(U[mu, s]))
+            Qfd = np.zeros((3, 3), dtype=np.complex128)
+            for a in range(8):
+                vals = []
+                for sg in (+1, -1):
+                    Up = U.copy()
+                    Up[mu, s] = O.expm(sg * h * T[a]) @ U[mu, s]
+                    vals.append(_fd_action(L.to_lat(Up, dims), c0, c1))
+                Qfd += T[a] * (vals[0] - vals[1]) / (2 * h)
+            worst = max(worst, float(np.abs(Q - Qfd).max()))
+    assert worst < 2e-6, worst
+
+
 # --------------------------------------------------------------------------
 # Exponential
 # --------------------------------------------------------------------------
