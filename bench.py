@@ -451,11 +451,13 @@ def run_serving(vs, device, args):
                    "eps=-0.25, w=0.02, VP, FP32, Poisson arrivals (seed 99), job seeds 100-163"}
 
 
-def cpu_baseline(args, vs=None, ctx=None, stream=None):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: one
-    annealed sweep of the 32^3 x 64 field (8.4M link updates) from iid uniform
-    Z(3) labels (the cooled-and-projected hot start has uniform label marginals),
-    after the centrifuge.  Returns link-updates/s on the host cores."""
+def cpu_baseline(args, vs=None, ctx=None, stream=None, sweeps=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    `sweeps` annealed sweeps (default --cpu-sweeps) of the 32^3 x 64 field
+    (8.4M link updates each) from iid uniform Z(3) labels (the
+    cooled-and-projected hot start has uniform label marginals), after the
+    centrifuge.  Returns link-updates/s on the host cores."""
+    n_sw = args.cpu_sweeps if sweeps is None else sweeps
     import oracle as O
     import synth
     V = int(np.prod(DIMS))
@@ -463,19 +465,19 @@ def cpu_baseline(args, vs=None, ctx=None, stream=None):
     Uc = O.centrifuge(DIMS, lab, OMEGA, CENTRIFUGE_SEED)
     nt = O.max_threads()
     t0 = time.perf_counter()
-    U1, rej = O.smooth(DIMS, Uc, lab, args.cpu_sweeps, RHO, eps=EPS, vp=True, nthreads=nt)
+    U1, rej = O.smooth(DIMS, Uc, lab, n_sw, RHO, eps=EPS, vp=True, nthreads=nt)
     dt = time.perf_counter() - t0
-    out = {"value": 4 * V * args.cpu_sweeps / dt, "unit": "link-updates/s", "cores": nt,
+    out = {"value": 4 * V * n_sw / dt, "unit": "link-updates/s", "cores": nt,
            "kind": "oracle",
            "sample": "%d annealed over-improved sweep(s) of the 32^3x64 field from iid uniform "
                      "Z(3) labels (seed 3) after the centrifuge, FP64, OpenMP over the sites of "
-                     "a colour class" % args.cpu_sweeps, "seconds": dt}
+                     "a colour class" % n_sw, "seconds": dt}
     if vs is not None:
         # error of the FP32 GPU path against the oracle on the same sample
         f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK18, stream)
         vs.vs_load_field(f, labels=lab)
         vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
-        st = vs.vs_smooth(f, args.cpu_sweeps, RHO, EPS, U0, vortex_preserve=True, stats=True,
+        st = vs.vs_smooth(f, n_sw, RHO, EPS, U0, vortex_preserve=True, stats=True,
                           reunit_every=REUNIT)
         Ug = vs.vs_read_field(f)
         vs.vs_field_destroy(f)
@@ -491,10 +493,10 @@ def run_reference(args):
         return
     t0 = time.perf_counter()
     for _ in range(min(args.warmup, 1)):
-        cpu_baseline(args)
+        cpu_baseline(args, sweeps=args.ref_sweeps)
     vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args))
+        vals.append(cpu_baseline(args, sweeps=args.ref_sweeps))
     v = statistics.median([x["value"] for x in vals])
     cb = dict(vals[-1])
     cb["value"] = v
@@ -561,7 +563,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweeps", type=int, default=N_SWEEPS)
     ap.add_argument("--fp64-sweeps", type=int, default=10)
-    ap.add_argument("--cpu-sweeps", type=int, default=1)
+    ap.add_argument("--cpu-sweeps", type=int, default=2,
+                    help="oracle sweeps in the cpu_baseline leg (about 11 s on 16 Arm cores)")
+    ap.add_argument("--ref-sweeps", type=int, default=1,
+                    help="oracle sweeps per step of --impl reference")
     ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--serve-rate", type=float, default=12.0)
     ap.add_argument("--no-fp64", action="store_true")
