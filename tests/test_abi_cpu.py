@@ -102,3 +102,22 @@ def test_binding_checks_buffers_before_the_call(libvs):
     a = np.zeros((4, V, 3, 3, 2))
     assert vs._host_links(a) is a
     assert vs._host_links(np.zeros((4, V, 3, 3), np.complex64)).dtype == np.complex128
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No fallback: with no libvs.so where the binding looks, importing it
+    raises ImportError naming the missing library, and the product package
+    never imports the oracle."""
+    import subprocess
+    import sys
+    env = dict(os.environ, VS_BUILD_DIR=str(tmp_path / "empty"))
+    r = subprocess.run([sys.executable, "-c", "import paper_2203_09764_gb300.vs"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libvs.so is not built" in r.stderr
+    r = subprocess.run([sys.executable, "-c",
+                        "import sys, paper_2203_09764_gb300.vs; "
+                        "print(sorted(m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')))"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "[]"
