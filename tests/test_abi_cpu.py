@@ -121,3 +121,35 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
                        cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == "[]"
+
+
+def test_oracle_and_product_share_no_code():
+    """The oracle and the GPU path are independent: no include or import
+    crosses between oracle/ and the product (csrc, include/, the binding),
+    and the shared seeded input generators (synth/) import neither."""
+    import glob
+    inc = re.compile(r'^\s*#\s*include\s*[<"]([^>"]+)[>"]', re.M)
+    imp = re.compile(r"^\s*(?:from|import)\s+([A-Za-z_][\w.]*)", re.M)
+
+    def text(p):
+        with open(p) as f:
+            return f.read()
+
+    product_c = glob.glob(os.path.join(ROOT, "paper_2203_09764_gb300", "csrc", "*"))
+    product_c += glob.glob(os.path.join(ROOT, "include", "*.h"))
+    for p in product_c:
+        for h in inc.findall(text(p)):
+            assert "oracle" not in h, (p, h)
+    for p in glob.glob(os.path.join(ROOT, "oracle", "*.c")):
+        for h in inc.findall(text(p)):
+            assert not any(k in h for k in ("vs.h", "csrc", "paper_2203", ".cuh", "vs_")), (p, h)
+    for p in glob.glob(os.path.join(ROOT, "paper_2203_09764_gb300", "*.py")):
+        for m in imp.findall(text(p)):
+            assert not (m == "oracle" or m.startswith("oracle.")), (p, m)
+    for p in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        for m in imp.findall(text(p)):
+            assert not m.startswith("paper_2203_09764_gb300"), (p, m)
+    for p in glob.glob(os.path.join(ROOT, "synth", "*.py")):
+        for m in imp.findall(text(p)):
+            assert not (m.startswith("oracle") or m.startswith("paper_2203_09764_gb300")), (p, m)
+    assert product_c and glob.glob(os.path.join(ROOT, "oracle", "*.c"))
