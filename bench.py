@@ -314,6 +314,11 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline(args, vs, ctx, stream)
         except Exception as e:
             line["cpu_baseline"] = {"error": repr(e)}
+        else:
+            try:
+                line["cpu_baseline"]["single_core"] = oracle_single_core()
+            except Exception as e:
+                line["cpu_baseline"]["single_core"] = {"error": repr(e)}
 
     vs.vs_destroy(ctx)
     if rank == 0:
@@ -484,6 +489,24 @@ def cpu_baseline(args, vs=None, ctx=None, stream=None, sweeps=None):
         out["fp32_max_link_err_vs_oracle"] = float(np.abs(Ug - U1).max())
         out["reject_counts_equal"] = [s["n_reject"] for s in st] == list(rej)
     return out
+
+
+def oracle_single_core():
+    """The FP64 oracle, as it stands, on one host core: one annealed
+    over-improved sweep of a 16^3 x 32 field of the same recipe (524,288
+    link updates; the cost per link does not depend on the lattice size)."""
+    import oracle as O
+    import synth
+    dims = (16, 16, 16, 32)
+    V = int(np.prod(dims))
+    lab = synth.iid_labels(dims, 3, p0=1 / 3, p_plus=1 / 3)
+    Uc = O.centrifuge(dims, lab, OMEGA, CENTRIFUGE_SEED)
+    t0 = time.perf_counter()
+    O.smooth(dims, Uc, lab, 1, RHO, eps=EPS, vp=True, nthreads=1)
+    dt = time.perf_counter() - t0
+    return {"value": 4 * V / dt, "unit": "link-updates/s", "cores": 1,
+            "sample": "1 annealed over-improved sweep of a 16^3x32 field from iid uniform Z(3) labels "
+                      "(seed 3) after the centrifuge, FP64, one thread", "seconds": dt}
 
 
 def run_reference(args):
