@@ -78,14 +78,20 @@ def test_label_matches_nearest_centre_on_haar_matrices():
 # Staples and the stout generator, Eqs. (plaq_staples), (generator), (over-improvement)
 # --------------------------------------------------------------------------
 
+def _printed(name):
+    with open(os.path.join(GOLDEN, "paper_printed_values.json")) as f:
+        return json.load(f)[name]
+
+
 def test_overimproved_coefficients_and_alpha_min():
     # eps = 1 is standard smearing (Sec. III): rectangles drop out.
     assert O.overimproved_coeffs(1.0, 1.0) == (1.0, 0.0)
     # alpha_min from the extremal staples (S = -3, R = 18, Appendix B):
-    # Re L1 = (1 - a) + a/6 (c0 S + c1 R) < 0.  The paper prints 0.4486 at eps = -0.25.
-    c0, c1 = O.overimproved_coeffs(-0.25, 1.0)
+    # Re L1 = (1 - a) + a/6 (c0 S + c1 R) < 0, against the value the paper prints.
+    g = _printed("alpha_min")
+    c0, c1 = O.overimproved_coeffs(g["epsilon"], g["u0"])
     amin = 1.0 / (1.0 - (c0 * -3.0 + c1 * 18.0) / 6.0)
-    assert abs(amin - 0.4486) < 5e-5
+    assert abs(amin - g["value"]) <= 0.5 * 10.0 ** -g["printed_decimals"]
     # and the paper's closed form, Eq. (alpha_condition_ape), for other eps, u0
     for eps, u0 in [(-2.5, 1.0), (-1.0, 0.9), (0.0, 0.85), (0.5, 1.0)]:
         c0, c1 = O.overimproved_coeffs(eps, u0)
@@ -125,7 +131,9 @@ def test_staple_sum_example_two_identity_four_centre():
         U = O.links_from_labels(dims, lab)
         S = O.staple_sum(dims, U, mu, tuple(x), 1.0, 0.0)
         assert np.allclose(S, 1j * n * 2 * np.sqrt(3) * np.eye(3), atol=1e-13)
-        assert abs(S[0, 0].imag - n * 3.464) < 1e-3
+        g = _printed("staple_two_identity_four_centre")
+        assert abs(abs(S[0, 0].imag) - g["abs_s"]) <= 0.5 * 10.0 ** -g["printed_decimals"]
+        assert abs(S[0, 0].real) < 1e-13
 
 
 def test_staple_gauge_covariance():
