@@ -14,7 +14,7 @@ __all__ = [
     "build_oracle", "lib", "max_threads", "use_library", "compile_variant", "source",
     "label_matrix", "labels", "links_from_labels", "splitmix64", "centrifuge_pair",
     "centrifuge", "overimproved_coeffs", "staple_sum", "expm", "stout_generator",
-    "colour", "smooth", "action", "centre_charges", "vortex_check", "gauge_transform",
+    "colour", "smooth", "action", "centre_charges", "vortex_check", "correlation", "gauge_transform",
     "cool", "aus", "maxretr", "observables", "reunit", "ucp", "ape_ucp", "flow_rk3", "ANNEALED", "SIMULTANEOUS",
 ]
 
@@ -107,7 +107,8 @@ def _declare(L):
                                      ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, P]),
         "or_action": (ctypes.c_int, [P, P, P, P]),
         "or_centre_charges": (ctypes.c_int, [P, P, P]),
-        "or_vortex_check": (ctypes.c_int, [P, P, P, P, P, P, P]),
+        "or_vortex_check": (ctypes.c_int, [P, P, P, P, P, P, P, dbl, P]),
+        "or_correlation": (ctypes.c_int, [ctypes.c_long, P, P, P]),
         "or_gauge_transform": (ctypes.c_int, [P, P, P]),
         "or_cool": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "or_aus": (ctypes.c_int, [P, P, P, ctypes.c_int, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
@@ -278,17 +279,34 @@ def centre_charges(dims, lab):
     return ch
 
 
-def vortex_check(dims, links, ref_labels, gauge=None):
+def vortex_check(dims, links, ref_labels, gauge=None, near_tol=1e-5):
+    """Label and centre-charge differences against ref_labels, the smallest
+    angular margin of arg Tr U from a sector edge, and the number of links
+    with a margin below near_tol."""
     d = _dims(dims)
     U = _c128(links)
     ref = np.ascontiguousarray(ref_labels, dtype=np.int8)
     nd = ctypes.c_int64()
     nc = ctypes.c_int64()
+    nn = ctypes.c_int64()
     mm = ctypes.c_double()
     G = None if gauge is None else _c128(gauge)
     _check(lib().or_vortex_check(_p(d), _p(U), _p(ref), ctypes.byref(nd), ctypes.byref(nc),
-                                 ctypes.byref(mm), _p(G) if G is not None else None), "vortex_check")
-    return dict(n_label_diff=nd.value, n_charge_diff=nc.value, min_margin=mm.value)
+                                 ctypes.byref(mm), _p(G) if G is not None else None,
+                                 float(near_tol), ctypes.byref(nn)), "vortex_check")
+    return dict(n_label_diff=nd.value, n_charge_diff=nc.value, min_margin=mm.value,
+                n_near_boundary=nn.value)
+
+
+def correlation(a, b):
+    """C_XY of two per-site densities (Sec. VII, Eq. correlation_s)."""
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+    if a.size != b.size:
+        raise ValueError("densities of different sizes")
+    C = ctypes.c_double()
+    _check(lib().or_correlation(a.size, _p(a), _p(b), ctypes.byref(C)), "correlation")
+    return C.value
 
 
 def gauge_transform(dims, links, G):

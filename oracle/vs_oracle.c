@@ -148,7 +148,8 @@ static int label_of_trace(cplx t) {
     return arg > 0.0 ? +1 : -1;
 }
 
-/* Angular distance of arg Tr M from the nearest sector boundary. */
+/* Angular distance of arg Tr M from the nearest sector boundary: the sector
+ * edges of Eq. (centre_element) lie at arg = pi/3, -pi/3 and pi (= -pi). */
 static double margin_of_trace(cplx t) {
     double a = creal(t), b = cimag(t) + 0.0;
     double arg = atan2(b, a);
@@ -665,11 +666,12 @@ int or_centre_charges(const int32_t dims[4], const int8_t *labels, int8_t *charg
 
 /* Counts over the field: links whose label differs from the reference, and
  * plaquettes whose centre charge differs from the reference charge; plus the
- * smallest angular distance of any arg Tr U from a sector boundary.  With a
+ * smallest angular distance of any arg Tr U from a sector boundary and
+ * (optional) the number of links closer than near_tol to one.  With a
  * gauge transformation G the labels are those of G^dag(x) U G(x+mu). */
 int or_vortex_check(const int32_t dims[4], const double *links, const int8_t *ref_labels,
                     int64_t *n_label_diff, int64_t *n_charge_diff, double *min_margin,
-                    const double *gauge) {
+                    const double *gauge, double near_tol, int64_t *n_near_boundary) {
     lattice g;
     if (lat_init(&g, dims)) return -1;
     int8_t *lab = (int8_t *)malloc(4 * g.V);
@@ -685,10 +687,11 @@ int or_vortex_check(const int32_t dims[4], const double *links, const int8_t *re
             lab[(long)mu * g.V + s] = (int8_t)label_of_trace(tr);
             mar[(long)mu * g.V + s] = margin_of_trace(tr);
         }
-    int64_t nd = 0, nc = 0;
+    int64_t nd = 0, nc = 0, nn = 0;
     double mm = 1e300;
     for (long i = 0; i < 4 * g.V; ++i) {
         nd += lab[i] != ref_labels[i];
+        nn += mar[i] < near_tol;
         if (mar[i] < mm) mm = mar[i];
     }
     for (long s = 0; s < g.V; ++s) {
@@ -701,8 +704,31 @@ int or_vortex_check(const int32_t dims[4], const double *links, const int8_t *re
     *n_label_diff = nd;
     *n_charge_diff = nc;
     *min_margin = mm;
+    if (n_near_boundary) *n_near_boundary = nn;
     free(lab);
     free(mar);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Correlation of two densities, Sec. VII Eq. (correlation_s) and the C^q   */
+/* equation that follows it                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* C_XY = <a(x) b(x)> / (sqrt<a(x)^2> sqrt<b(x)^2>), <.> the mean over the n
+ * sites.  The paper's form is not mean-subtracted: the densities themselves
+ * are correlated.  Returns -2 when either density is zero everywhere. */
+int or_correlation(long n, const double *a, const double *b, double *C) {
+    if (n < 1 || !a || !b || !C) return -1;
+    double sab = 0.0, saa = 0.0, sbb = 0.0;
+    for (long i = 0; i < n; ++i) {
+        sab += a[i] * b[i];
+        saa += a[i] * a[i];
+        sbb += b[i] * b[i];
+    }
+    if (!(saa > 0.0) || !(sbb > 0.0)) return -2;
+    const double mab = sab / (double)n, maa = saa / (double)n, mbb = sbb / (double)n;
+    *C = mab / (sqrt(maa) * sqrt(mbb));
     return 0;
 }
 

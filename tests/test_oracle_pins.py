@@ -78,6 +78,69 @@ def test_label_matches_nearest_centre_on_haar_matrices():
     assert all(abs(f - 1 / 3) < 0.003 for f in frac)
 
 
+def _links_with_trace_angles(thetas):
+    """A (1,1,1,n/4) field whose link k is 2 exp(i theta_k) diag(1, 0, 0):
+    its trace sits at the angle theta_k exactly (up to the rounding of exp)."""
+    t = 2.0 * np.exp(1j * np.asarray(thetas, dtype=np.float64))
+    n = t.size
+    assert n % 4 == 0
+    M = np.zeros((n, 3, 3), dtype=np.complex128)
+    M[:, 0, 0] = t
+    return (1, 1, 1, n // 4), M.reshape(4, n // 4, 3, 3)
+
+
+def test_margin_of_trace_at_known_angles():
+    """The angular margin of arg Tr U from the nearest sector edge (pi/3,
+    -pi/3, pi) on traces placed at known distances from every edge, on both
+    sides, and at the sector centres (margin pi/3)."""
+    thetas, want = [], []
+    for d in (1e-9, 1e-6, 1e-3, 0.1, 0.5):
+        for edge, sides in ((np.pi / 3, (1, -1)), (-np.pi / 3, (1, -1)), (np.pi, (-1,)), (-np.pi, (1,))):
+            for sgn in sides:
+                thetas.append(edge + sgn * d)
+                want.append(d)
+    for c in (0.0, 2 * np.pi / 3, -2 * np.pi / 3):
+        thetas.append(c)
+        want.append(np.pi / 3)
+    while len(thetas) % 4:
+        thetas.append(0.0)
+        want.append(np.pi / 3)
+    dims, U = _links_with_trace_angles(thetas)
+    _, mar = O.labels(dims, U, with_margin=True)
+    got = mar.reshape(-1)
+    assert np.abs(got - np.asarray(want)).max() < 1e-12
+
+
+def test_margin_equals_half_width_minus_offset_from_sector_centre():
+    """Second formulation on Haar matrices: a trace in the sector of centre
+    element n lies at the angle phi = arg(Tr U e^{-2 pi i n/3}) from the sector
+    centre, and the sector is 2 pi/3 wide, so its margin is pi/3 - |phi|."""
+    n = 100_000
+    U = _rand_su3(n, seed=12)
+    t = np.trace(U, axis1=1, axis2=2)
+    dims = (1, 1, 1, n // 4)
+    _, mar = O.labels(dims, U.reshape(4, n // 4, 3, 3), with_margin=True)
+    c = L.label_nearest_centre(t)
+    phi = np.angle(t * np.exp(-2j * np.pi * c / 3))
+    assert np.abs(mar.reshape(-1) - (np.pi / 3 - np.abs(phi))).max() < 1e-12
+
+
+def test_vortex_check_counts_links_near_a_sector_edge():
+    """Links placed 1e-7, 5e-6, 2e-5 and 1e-3 rad from an edge: with a near
+    tolerance of 1e-5 rad exactly the first two of each are counted, and the
+    minimum margin is the closest one's."""
+    thetas = []
+    for edge in (np.pi / 3, -np.pi / 3, np.pi):
+        for d in (1e-7, 5e-6, 2e-5, 1e-3):
+            thetas.append(edge - d if edge == np.pi else edge + d)
+    dims, U = _links_with_trace_angles(thetas)
+    lab = O.labels(dims, U)
+    chk = O.vortex_check(dims, U, lab, near_tol=1e-5)
+    assert chk["n_near_boundary"] == 6
+    assert abs(chk["min_margin"] - 1e-7) < 1e-12
+    assert chk["n_label_diff"] == 0
+
+
 # --------------------------------------------------------------------------
 # Staples and the stout generator, Eqs. (plaq_staples), (generator), (over-improvement)
 # --------------------------------------------------------------------------
@@ -1081,3 +1144,27 @@ def test_periodic_extension_repeats_the_result():
         assert np.array_equal(big, rep(small))
         if rej_small is not None:
             assert int(rej_big.sum()) == int(rej_small.sum()) * int(np.prod(reps))
+
+
+# --------------------------------------------------------------------------
+# Correlation of densities, Sec. VII Eq. (correlation_s)
+# --------------------------------------------------------------------------
+
+def test_correlation_closed_forms():
+    """C(a, c a) = sign(c); symmetry; Cauchy-Schwarz; two phase-shifted
+    cosines over whole periods give cos(phase); with a constant offset the
+    paper's (not mean-subtracted) form gives (2 + cos phase) / 3."""
+    rng = np.random.default_rng(21)
+    a = rng.normal(size=4096) + 0.3
+    b = rng.normal(size=4096) - 0.1
+    assert abs(O.correlation(a, 2.5 * a) - 1) < 1e-14
+    assert abs(O.correlation(a, -0.7 * a) + 1) < 1e-14
+    assert O.correlation(a, b) == O.correlation(b, a)
+    assert abs(O.correlation(a, b)) < 1
+    n = 1000
+    x = 2 * np.pi * 3 * np.arange(n) / n
+    for ph in (0.0, 0.4, np.pi / 2, 2.0, np.pi):
+        assert abs(O.correlation(np.cos(x), np.cos(x + ph)) - np.cos(ph)) < 1e-13
+        assert abs(O.correlation(1 + np.cos(x), 1 + np.cos(x + ph)) - (2 + np.cos(ph)) / 3) < 1e-13
+    with pytest.raises(ValueError):
+        O.correlation(np.zeros(8), np.ones(8))
