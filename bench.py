@@ -361,26 +361,34 @@ def storage12(vs, ctx, stream, labels_dev, args, world, dev, peaks):
 
 
 def fp64_plain(vs, ctx, stream, labels_dev, args, value, world, dev):
-    """The same path with FP64 links and arithmetic, timed over a few sweeps."""
+    """The FP32 ratio over the GPU FP64 plain path on one scope: the same
+    sweeps (vs_smooth of --fp64-sweeps annealed over-improved VP sweeps, with
+    the FP32 re-unitarisation every 10, from the same centrifuged field after
+    one untimed sweep), timed with CUDA events in both precisions."""
     import torch
     n_links = 4 * int(np.prod(DIMS))
-    f64 = vs.vs_field_create(ctx, DIMS, vs.VS_FP64, vs.VS_LINK18, stream)
-    vs.vs_load_field(f64, labels=labels_dev)
-    vs.vs_centrifuge(f64, OMEGA, CENTRIFUGE_SEED)
-    vs.vs_smooth(f64, 1, RHO, EPS, U0, vortex_preserve=True)
-    torch.cuda.synchronize(dev)
-    n64 = args.fp64_sweeps
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    vs.vs_smooth(f64, n64, RHO, EPS, U0, vortex_preserve=True)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms64 = e0.elapsed_time(e1)
-    vs.vs_field_destroy(f64)
-    v64 = world * n_links * n64 / (ms64 / 1e3)
-    return {"value": v64, "unit": "link-updates/s", "sweeps": n64, "ms": ms64,
-            "fp32_over_fp64": value / v64}
+    n = args.fp64_sweeps
+    ms = {}
+    for name, prec in (("fp64", vs.VS_FP64), ("fp32", vs.VS_FP32)):
+        f = vs.vs_field_create(ctx, DIMS, prec, vs.VS_LINK18, stream)
+        vs.vs_load_field(f, labels=labels_dev)
+        vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+        vs.vs_smooth(f, 1, RHO, EPS, U0, reunit_every=REUNIT, vortex_preserve=True)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vs.vs_smooth(f, n, RHO, EPS, U0, reunit_every=REUNIT, vortex_preserve=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms[name] = e0.elapsed_time(e1)
+        vs.vs_field_destroy(f)
+    v64 = world * n_links * n / (ms["fp64"] / 1e3)
+    v32 = world * n_links * n / (ms["fp32"] / 1e3)
+    return {"value": v64, "unit": "link-updates/s", "sweeps": n, "ms": ms["fp64"],
+            "fp32_same_scope": {"value": v32, "ms": ms["fp32"]}, "fp32_over_fp64": v32 / v64,
+            "scope": "vs_smooth sweeps alone in both precisions (class updates, and FP32 "
+                     "re-unitarisation every 10 sweeps), same field and sweep count"}
 
 
 def other_paths(vs, ctx, stream, labels_dev, args, world, dev):
@@ -456,27 +464,36 @@ def run_serving(vs, device, args):
                    "eps=-0.25, w=0.02, VP, FP32, Poisson arrivals (seed 99), job seeds 100-163"}
 
 
-def cpu_baseline(args, vs=None, ctx=None, stream=None, sweeps=None):
+def oracle_input():
+    """The benchmark's input built by the oracle (same recipe and seed as the
+    GPU arm's vs_load_cooled: Haar SU(3) seed 3, 20 MaxReTr cooling sweeps,
+    Z(3) projection), centrifuged; cached on disk after the first build."""
+    import oracle as O
+    t0 = time.perf_counter()
+    lab = O.cooled_labels(DIMS, 3, N_COOL)
+    Uc = O.centrifuge(DIMS, lab, OMEGA, CENTRIFUGE_SEED)
+    return lab, Uc, time.perf_counter() - t0
+
+
+def cpu_baseline(args, vs=None, ctx=None, stream=None, sweeps=None, inp=None):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    `sweeps` annealed sweeps (default --cpu-sweeps) of the 32^3 x 64 field
-    (8.4M link updates each) from iid uniform Z(3) labels (the
-    cooled-and-projected hot start has uniform label marginals), after the
-    centrifuge.  Returns link-updates/s on the host cores."""
+    `sweeps` annealed sweeps (default --cpu-sweeps) of the 32^3 x 64 cooled
+    hot start (8.4M link updates each) after the centrifuge.  Returns
+    link-updates/s on the host cores."""
     n_sw = args.cpu_sweeps if sweeps is None else sweeps
     import oracle as O
-    import synth
     V = int(np.prod(DIMS))
-    lab = synth.iid_labels(DIMS, 3, p0=1 / 3, p_plus=1 / 3)
-    Uc = O.centrifuge(DIMS, lab, OMEGA, CENTRIFUGE_SEED)
+    lab, Uc, t_input = inp if inp is not None else oracle_input()
     nt = O.max_threads()
     t0 = time.perf_counter()
     U1, rej = O.smooth(DIMS, Uc, lab, n_sw, RHO, eps=EPS, vp=True, nthreads=nt)
     dt = time.perf_counter() - t0
     out = {"value": 4 * V * n_sw / dt, "unit": "link-updates/s", "cores": nt,
            "kind": "oracle",
-           "sample": "%d annealed over-improved sweep(s) of the 32^3x64 field from iid uniform "
-                     "Z(3) labels (seed 3) after the centrifuge, FP64, OpenMP over the sites of "
-                     "a colour class" % n_sw, "seconds": dt}
+           "sample": "%d annealed over-improved sweep(s) of the 32^3x64 cooled hot start (Haar SU(3) "
+                     "seed 3, 20 oracle MaxReTr cooling sweeps, Z(3) projection) after the "
+                     "centrifuge, FP64, OpenMP over the sites of a colour class" % n_sw,
+           "seconds": dt, "input_build_s": t_input}
     if vs is not None:
         # error of the FP32 GPU path against the oracle on the same sample
         f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK18, stream)
@@ -510,31 +527,41 @@ def oracle_single_core():
 
 
 def run_reference(args):
+    """The FP64 oracle on the benchmark's workload: each step is a bounded
+    sample of it, --ref-sweeps annealed sweeps of the centrifuged cooled
+    32^3 x 64 field; ms_per_step is the measured time of those sweeps."""
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
     if world > 1 and rank != 0:
         return
     t0 = time.perf_counter()
+    inp = oracle_input()
     for _ in range(min(args.warmup, 1)):
-        cpu_baseline(args, sweeps=args.ref_sweeps)
+        cpu_baseline(args, sweeps=args.ref_sweeps, inp=inp)
     vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args, sweeps=args.ref_sweeps))
+        vals.append(cpu_baseline(args, sweeps=args.ref_sweeps, inp=inp))
     v = statistics.median([x["value"] for x in vals])
+    step_ms = statistics.median([x["seconds"] for x in vals]) * 1e3
     cb = dict(vals[-1])
     cb["value"] = v
     line = {"metric": METRIC, "value": v, "unit": "link-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 4 * int(np.prod(DIMS)) * args.sweeps / v * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "32^3x64 over-improved stout eps=-0.25 rho=0.06, annealed, VP, "
-                                   "centrifuge w=0.02 (FP64 CPU oracle, timed on a bounded sample; "
-                                   "ms_per_step extrapolated to %d sweeps)" % args.sweeps,
-                       "lattice": list(DIMS), "sweeps": args.sweeps},
+            "config": {"workload": "32^3x64 cooled hot start (Haar SU(3) seed 3, 20 MaxReTr cooling "
+                                   "sweeps, Z(3) projection, built by the oracle); centrifuge w=0.02; "
+                                   "over-improved stout eps=-0.25 rho=0.06 u0=1, annealed, with vortex "
+                                   "preservation; FP64 CPU oracle, each step %d sweep(s) of the "
+                                   "workload's %d" % (args.ref_sweeps, args.sweeps),
+                       "lattice": list(DIMS), "sweeps": args.ref_sweeps},
+            "extrapolated_ms_per_workload_step": {
+                "value": 4 * int(np.prod(DIMS)) * args.sweeps / v * 1e3, "sweeps": args.sweeps,
+                "note": "not timed: the measured rate applied to the whole %d-sweep step" % args.sweeps},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "link-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
+            "input_build_s": inp[2],
             "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
 
@@ -601,7 +628,14 @@ def main():
     ap.add_argument("--other-sweeps", type=int, default=10)
     ap.add_argument("--scaling", action="store_true",
                     help="lattice-size sweep 16^3x32 .. 48^3x96 instead of the benchmark step")
+    ap.add_argument("--lattice", default=None,
+                    help="Lx,Ly,Lz,Lt of the workload (default 32,32,32,64), e.g. a small lattice "
+                         "for a quick check of the output")
     args = ap.parse_args()
+    if args.lattice:
+        global DIMS
+        DIMS = tuple(int(v) for v in args.lattice.split(","))
+        assert len(DIMS) == 4 and all(d > 0 and d % 4 == 0 for d in DIMS), "extents: positive multiples of 4"
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -141,6 +141,19 @@ typedef struct {
     double action;                /* <S>/beta after the sweep, when recorded */
     int32_t has_action;
     int32_t n_singular;           /* vs_smooth_ape: blocked matrices with no projection (link kept) */
+    /* Vortex-preservation diagnostics (Sec. VI; the n_diff counts of the
+     * paper's tables) of vs_smooth, vs_smooth_aus and vs_smooth_ape; -1 / NaN
+     * from vs_flow_rk3: */
+    int64_t n_label_diff;         /* candidates whose Z(3) label (Sec. I) differs from the reference label;
+                                     with vortex preservation these are the rejections, without it the
+                                     label differences after the sweep */
+    int64_t n_undecidable;        /* candidates whose trace lies within the precision's rounding band of a
+                                     sector edge (FP32: 2e-6, FP64: 1e-12, in trace units), where another
+                                     rounding of the same arithmetic could decide the test differently;
+                                     outside it the decision equals that of exact arithmetic on the
+                                     stored links */
+    double min_margin;            /* smallest angular distance of a candidate's arg Tr from a sector edge
+                                     (radians) */
 } vs_sweep_stats;
 
 /* n_sweeps of stout smoothing, Eqs. (stout)/(generator), with
@@ -234,38 +247,66 @@ typedef struct {
 vs_status vs_observables(vs_field *f, vs_observables_out *out, double *S_site, double *SR_site,
                          double *q_site, int32_t where);
 
+/* Correlation of two per-site densities, Sec. VII Eq. (correlation_s) and the
+ * C^q equation after it:
+ *   C_XY = <a(x) b(x)> / (sqrt<a(x)^2> sqrt<b(x)^2>),
+ * <.> the mean over the field's V sites (the paper's form: not
+ * mean-subtracted).  a, b: double [V] (any site order, the same for both; e.g.
+ * the lexicographic densities of vs_observables of two smoothed fields of
+ * this field's dims), host or device per `where`; the field supplies the
+ * lattice size, the stream and (for host input) its staging buffer.  Sums in
+ * FP64 in a fixed order.  Synchronous.  EINVAL: NULL arguments, bad `where`,
+ * a density that is zero on every site. */
+vs_status vs_correlation(vs_field *f, const double *a, const double *b, int32_t where, double *C);
+
 /* Vortex-structure check of the current field against the reference. Synchronous. */
 vs_status vs_vortex_check(vs_field *f, vs_vortex_report *out);
 
-/* Vortex check that allocates nothing.  The paper has no counterpart: this
- * is a service for callers that cannot allocate device memory at the point
- * where they need the check -- code running while a CUDA graph is being
- * captured on another stream of the thread (the global capture mode forbids
- * allocating and synchronising calls), a serving loop under a hard memory cap
- * that must not call into cudaMalloc (which can block on the whole device or
- * fail under pressure), or a host that hands the library preallocated buffers
- * and forbids any other allocation.  It runs the same kernels as
- * vs_vortex_check on buffers the caller owns: links and ref_labels are device
- * pointers in the layout of a field with these dims, precision and storage
- * (vs_field_describe gives them); the result goes to the caller's host struct.
- * Its scratch (one byte per link plus eight counters) is a fixed array of
- * VS_NOALLOC_MAX_LINKS bytes compiled into the library, which every GPU that
- * loads the library keeps until the process exits.  EINVAL for lattices with
- * more than VS_NOALLOC_MAX_LINKS links (2,097,152 sites, e.g. 32^3 x 64).  Runs
- * on the calling thread's current device, which must own the buffers.  The
- * first call on a device looks up the scratch there and pins a 64-byte mapped
- * host block, so make that first call before any capture.  The call waits for
- * its own work without a synchronising CUDA call: its last kernel writes the
- * report and a sequence number to the mapped block, which the host watches
- * (EDEVICE after 30 s without it).  Calls on one device are serialised, so
- * they never share the scratch on the GPU.  `stream`: where the kernels run;
- * while another stream captures, give a non-blocking stream (work on the
- * legacy default stream, NULL, synchronises with the blocking streams, which
- * a capture forbids). */
+/* Vortex check that allocates no device memory.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory at the point where they need the check -- code running while a CUDA
+ * graph is being captured on another stream of the thread (the global
+ * capture mode forbids allocating and synchronising calls), a serving loop
+ * under a hard memory cap that must not call into cudaMalloc (which can block
+ * on the whole device or fail under pressure), or a host that hands the
+ * library preallocated buffers and forbids any other allocation.  It runs the
+ * same kernels as vs_vortex_check on buffers the caller owns: links and
+ * ref_labels are device pointers in the layout of a field with these dims,
+ * precision and storage, and gauge is the field's random gauge transformation
+ * G (Sec. V.D; the test then runs in the original gauge, on G^dag(x) U
+ * G(x+mu), as vs_vortex_check does) or NULL for a field in its original gauge
+ * -- vs_field_describe gives all three.  The result goes to the caller's host
+ * struct.  Its scratch (one byte per link plus eight counters) is a fixed
+ * array of VS_NOALLOC_MAX_LINKS bytes compiled into the library, which every
+ * GPU that loads the library keeps until the process exits.  EINVAL for
+ * lattices with more than VS_NOALLOC_MAX_LINKS links (2,097,152 sites, e.g.
+ * 32^3 x 64).  Runs on the calling thread's current device, which must own
+ * the buffers.
+ *
+ * Once per device the library looks up the scratch there, loads the check's
+ * kernels and pins a 64-byte mapped host block (its only allocation, and on
+ * the host): vs_create does this for its device, vs_noalloc_prepare for any
+ * device, and otherwise the first call on a device does it (with the
+ * thread's capture mode relaxed for those calls, so a first call made while
+ * another stream captures neither fails nor invalidates the capture).  The
+ * call waits for its own work without a synchronising CUDA call: its last
+ * kernel writes the report and a sequence number to the mapped block, which
+ * the host watches.  Calls on one device are serialised on the host and
+ * share the scratch; one call's kernels finish before the next call on that
+ * device launches any, except after a call that gave up waiting (EDEVICE
+ * after 30 s without a result): its kernels may still be running, so later
+ * calls on that device return EBUSY until its result has been published.
+ * `stream`: where the kernels run; while another stream captures, give a
+ * non-blocking stream (work on the legacy default stream, NULL, synchronises
+ * with the blocking streams, which a capture forbids). */
 #define VS_NOALLOC_MAX_LINKS (8 * 1024 * 1024)
-vs_status vs_vortex_check_noalloc(const void *links, const int8_t *ref_labels, const int32_t dims[4],
-                                  int32_t precision, int32_t storage, void *stream,
+vs_status vs_vortex_check_noalloc(const void *links, const int8_t *ref_labels, const void *gauge,
+                                  const int32_t dims[4], int32_t precision, int32_t storage, void *stream,
                                   vs_vortex_report *out);
+
+/* The once-per-device set-up of vs_vortex_check_noalloc, for a device on which
+ * no vs_create ran: afterwards its calls there allocate nothing at all. */
+vs_status vs_noalloc_prepare(int32_t device);
 
 /* Mean Wilson action density <S>/beta, Sec. V: (1/V) sum_x 1/72 sum_{mu != nu}
  * Re Tr(1 - P_munu(x)); products in the field precision, sums in FP64 with a
@@ -337,6 +378,9 @@ typedef struct {
                                       at (reals before it)*P, site i at w*i inside it */
     int8_t *labels;                /* device: [4][plane_stride] reference labels */
     void *stream;
+    void *gauge;                   /* device: the random gauge transformation G of vs_gauge_transform
+                                      (18 reals per site in the field precision, one plane group as
+                                      for direction 0 of the links), or NULL in the original gauge */
 } vs_field_desc;
 
 /* Device layout of a field.  Within a component plane the sites follow the

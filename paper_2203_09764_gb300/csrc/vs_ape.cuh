@@ -103,7 +103,7 @@ __device__ __forceinline__ bool ucp_project(const M3<T> &V, M3<T> &out) {
 // vortex-preservation test, store if accepted.
 template <class T, int NC, int MU>
 __device__ __forceinline__ void ape_finish(const ApeParams &a, const Pt &x, int i, M3<T> Vb, const M3<T> &u,
-                                           bool &reject, bool &singular) {
+                                           Update<T> &up) {
     const Geo &g = a.g;
     const T al = sizeof(T) == 4 ? T(a.alpha_f) : T(a.alpha);
     const T w6 = al / T(6), w1 = T(1) - al;
@@ -115,27 +115,14 @@ __device__ __forceinline__ void ape_finish(const ApeParams &a, const Pt &x, int 
     M3<T> un;
     if (!ucp_project<T>(Vb, un)) {
         un = u;
-        singular = true;
+        up.second = true;      // singular: counted in the second slot
     }
     if (NC == 12) rebuild_row2(un);
-    if (a.vp) {
-        T tr_re, tr_im;
-        vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, un, tr_re, tr_im);
-        reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
-    }
-    if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, un);
+    T tr_re, tr_im;
+    vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, un, tr_re, tr_im);
+    vp_decide<T>(a.vp, a.counters != nullptr, (int)a.ref[(long long)MU * g.P + i], tr_re, tr_im, up);
+    if (!up.reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, un);
     else if (a.U != a.Usrc) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, u);
-}
-
-__device__ __forceinline__ void ape_count(const ApeParams &a, bool reject, bool singular) {
-    if (a.counters) {
-        const unsigned rb = __ballot_sync(0xffffffffu, reject);
-        const unsigned sb = __ballot_sync(0xffffffffu, singular);
-        if ((threadIdx.x & 31) == 0) {
-            if (rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
-            if (sb) atomicAdd(&a.counters[1], (unsigned long long)__popc(sb));
-        }
-    }
 }
 
 // APE / AUS with unit circle projection: one thread per link of the colour
@@ -145,7 +132,7 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     k_ape(ApeParams a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false, singular = false;
+    Update<T> up;
     if (active) {
         const Geo &g = a.g;
         const Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
@@ -154,9 +141,9 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
         const M3<T> Vb = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
         const M3<T> u = load_link<T, NC>(Us, g.P, MU, i);
-        ape_finish<T, NC, MU>(a, x, i, Vb, u, reject, singular);
+        ape_finish<T, NC, MU>(a, x, i, Vb, u, up);
     }
-    ape_count(a, reject, singular);
+    count_update<T>(a.counters, up);
 }
 
 // FP32 over-improved AUS+UCP with the one-pass link stream of k_subsweep_fused.
@@ -167,7 +154,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeP
     float2 *ring2 = reinterpret_cast<float2 *>(ape_dyn + 6 * (NC / 4) * VS_RING_THREADS);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false, singular = false;
+    Update<float> up;
     if (active) {
         const Geo &g = a.g;
         const Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
@@ -176,9 +163,9 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeP
         M3<float> Ux;
         const M3<float> Vb =
             staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
-        ape_finish<float, NC, MU>(a, x, i, Vb, Ux, reject, singular);
+        ape_finish<float, NC, MU>(a, x, i, Vb, Ux, up);
     }
-    ape_count(a, reject, singular);
+    count_update<float>(a.counters, up);
 }
 
 // End of one Runge-Kutta stage for link (MU, i) from its staple sum sig and

@@ -81,6 +81,10 @@ extern "C" vs_status vs_create(const vs_options *opt, vs_ctx **out) {
     if (c->opt.max_slots <= 0) c->opt.max_slots = 8;
     if (c->opt.max_queue <= 0) c->opt.max_queue = 1024;
     c->t0 = std::chrono::steady_clock::now();
+    // the one-time set-up of vs_vortex_check_noalloc on this device, so that
+    // its later calls allocate nothing at all; a failure here is reported by
+    // the first such call instead
+    vs_noalloc_prepare(o.device);
     *out = c;
     return VS_OK;
 }
@@ -162,6 +166,7 @@ extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t p
     // scalars live after the partials: [1216 doubles][result double][counters...]
     f->d_result = f->partials + 1216;
     f->d_counts = (unsigned long long *)(f->d_result + 1);      // 8 slots
+    f->d_sweep = f->d_counts + 8;                               // kSweepSlots slots
     *out = f;
     return VS_OK;
 }
@@ -207,6 +212,7 @@ extern "C" vs_status vs_field_describe(const vs_field *f, vs_field_desc *d) {
     d->links = f->U;
     d->labels = f->ref;
     d->stream = (void *)f->stream;
+    d->gauge = f->gauge_on ? f->G : nullptr;
     return VS_OK;
 }
 
@@ -471,6 +477,30 @@ extern "C" vs_status vs_reunitarise(vs_field *f) {
 // Smoothing
 // ---------------------------------------------------------------------------
 
+// Angular margin from the smallest margin sine of a sweep (NaN: no candidate).
+static double margin_of_sine_bits(unsigned long long bits) {
+    if (bits == kMarginInit) return std::nan("");
+    double v;
+    memcpy(&v, &bits, sizeof v);
+    return std::asin(std::min(v, 1.0));
+}
+
+// The vortex-preservation diagnostics of one sweep's counters.
+static void fill_vp_stats(vs_sweep_stats &o, const unsigned long long *c) {
+    o.n_label_diff = (int64_t)c[kCntLabelDiff];
+    o.n_undecidable = (int64_t)c[kCntUndecidable];
+    o.min_margin = margin_of_sine_bits(c[kCntMarginSine]);
+}
+
+cudaError_t vs::init_sweep_counters(unsigned long long *c, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const size_t pitch = kSweepSlots * sizeof(unsigned long long);
+    cudaError_t e = cudaMemset2DAsync(c, pitch, 0, kCntMarginSine * sizeof(unsigned long long), n, st);
+    if (e == cudaSuccess)
+        e = cudaMemset2DAsync(c + kCntMarginSine, pitch, 0x7f, sizeof(unsigned long long), n, st);
+    return e;
+}
+
 static cudaError_t subsweep_launch(vs_field *f, bool rect, int mu, const SubsweepParams &p) {
     if (f->prec == VS_FP64) return launch_subsweep_d18(rect, mu, p, f->stream);
     if (f->nc == 12) return launch_subsweep_f12(rect, mu, p, f->stream);
@@ -517,8 +547,8 @@ extern "C" vs_status vs_subsweep(vs_field *f, int32_t mu, int32_t colour, double
     SubsweepParams p = make_params(f, rho, eps, u0, vp);
     p.colour = colour;
     p.n_threads = f->g.V / 4;
-    p.counters = f->d_counts;
-    CK(cudaMemsetAsync(f->d_counts, 0, 2 * sizeof(unsigned long long), f->stream));
+    p.counters = f->d_sweep;
+    CK(init_sweep_counters(f->d_sweep, 1, f->stream));
     CK(subsweep_launch(f, eps != 1.0, mu, p));
     return VS_OK;
 }
@@ -564,7 +594,7 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
         CK(cudaStreamSynchronize(f->stream));
         dev_free(f->ctx, f->sweep_counts);
         dev_free(f->ctx, f->sweep_actions);
-        f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, 2 * sizeof(unsigned long long) * n_sweeps);
+        f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, kSweepSlots * sizeof(unsigned long long) * n_sweeps);
         f->sweep_actions = (double *)dev_alloc(f->ctx, sizeof(double) * n_sweeps);
         if (!f->sweep_counts || !f->sweep_actions) {
             f->sweep_cap = 0;
@@ -572,8 +602,7 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
         }
         f->sweep_cap = n_sweeps;
     }
-    if (want_stats && n_sweeps > 0)
-        CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_sweeps, f->stream));
+    if (want_stats) CK(init_sweep_counters(f->sweep_counts, n_sweeps, f->stream));
     if (a.kind == VS_SIMULTANEOUS) {
         st = ensure_scratch(f, field_bytes(f));
         if (st) return st;
@@ -595,7 +624,7 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
         NvtxRange range("vs stout sweep");
         const double r = a.rho_per_sweep ? a.rho_per_sweep[s] : rho;
         SubsweepParams p = make_params(f, r, eps, u0, vp);
-        p.counters = fixed_counters ? fixed_counters : (want_stats ? f->sweep_counts + 2 * s : nullptr);
+        p.counters = fixed_counters ? fixed_counters : (want_stats ? f->sweep_counts + kSweepSlots * s : nullptr);
         if (f->profiling) CK(cudaEventRecord(f->events[2 * s], f->stream));
         if (a.kind == VS_ANNEALED) {
             p.n_threads = f->g.V / 4;
@@ -639,7 +668,7 @@ extern "C" vs_status vs_smooth(vs_field *f, int32_t n_sweeps, double rho, double
     if (!f) return fail(VS_EINVAL, "vs_smooth: NULL field");
     vs_status st = smooth_enqueue(f, n_sweeps, rho, eps, u0, sched, vp, stats != nullptr);
     if (st || !stats) return st;
-    std::vector<unsigned long long> cnt(2 * (size_t)n_sweeps);
+    std::vector<unsigned long long> cnt(kSweepSlots * (size_t)n_sweeps);
     std::vector<double> act(n_sweeps);
     if (n_sweeps > 0) {
         CK(cudaMemcpyAsync(cnt.data(), f->sweep_counts, cnt.size() * sizeof(unsigned long long),
@@ -651,10 +680,12 @@ extern "C" vs_status vs_smooth(vs_field *f, int32_t n_sweeps, double rho, double
     const long long per_sweep = 4ll * f->g.V;
     for (int s = 0; s < n_sweeps; ++s) {
         vs_sweep_stats &o = stats[s];
+        const unsigned long long *c = &cnt[kSweepSlots * (size_t)s];
         memset(&o, 0, sizeof o);
-        o.n_reject = (int64_t)cnt[2 * s];
+        o.n_reject = (int64_t)c[kCntReject];
         o.n_accept = per_sweep - o.n_reject;
-        o.n_fp64_exp = (int64_t)cnt[2 * s + 1];
+        o.n_fp64_exp = (int64_t)c[kCntSecond];
+        fill_vp_stats(o, c);
         int ae = f->last_action_every;
         if (ae > 0 && (s + 1) % ae == 0) {
             o.has_action = 1;
@@ -679,7 +710,7 @@ extern "C" vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, 
         CK(cudaStreamSynchronize(f->stream));
         dev_free(f->ctx, f->sweep_counts);
         dev_free(f->ctx, f->sweep_actions);
-        f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, 2 * sizeof(unsigned long long) * n_sweeps);
+        f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, kSweepSlots * sizeof(unsigned long long) * n_sweeps);
         f->sweep_actions = (double *)dev_alloc(f->ctx, sizeof(double) * n_sweeps);
         if (!f->sweep_counts || !f->sweep_actions) {
             f->sweep_cap = 0;
@@ -687,12 +718,11 @@ extern "C" vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, 
         }
         f->sweep_cap = n_sweeps;
     }
-    if (stats && n_sweeps > 0)
-        CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_sweeps, f->stream));
+    if (stats) CK(init_sweep_counters(f->sweep_counts, n_sweeps, f->stream));
     AusParams a = make_aus_params(f, alpha, epsilon, u0, n_hits, vortex_preserve);
     for (int s = 0; s < n_sweeps; ++s) {
         NvtxRange range("vs AUS sweep");
-        a.counters = stats ? f->sweep_counts + 2 * s : nullptr;
+        a.counters = stats ? f->sweep_counts + kSweepSlots * s : nullptr;
         for (int mu = 0; mu < 4; ++mu)
             for (int c = 0; c < 4; ++c) {
                 a.colour = c;
@@ -704,15 +734,16 @@ extern "C" vs_status vs_smooth_aus(vs_field *f, int32_t n_sweeps, double alpha, 
     }
     f->sweeps_done += n_sweeps;
     if (!stats) return VS_OK;
-    std::vector<unsigned long long> cnt(2 * (size_t)n_sweeps);
+    std::vector<unsigned long long> cnt(kSweepSlots * (size_t)n_sweeps);
     if (n_sweeps > 0)
         CK(cudaMemcpyAsync(cnt.data(), f->sweep_counts, cnt.size() * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, f->stream));
     CK(cudaStreamSynchronize(f->stream));
     for (int s = 0; s < n_sweeps; ++s) {
         memset(&stats[s], 0, sizeof stats[s]);
-        stats[s].n_reject = (int64_t)cnt[2 * s];
+        stats[s].n_reject = (int64_t)cnt[kSweepSlots * s + kCntReject];
         stats[s].n_accept = 4ll * f->g.V - stats[s].n_reject;
+        fill_vp_stats(stats[s], &cnt[kSweepSlots * s]);
     }
     return check_device_error(f);
 }
@@ -733,13 +764,13 @@ static cudaError_t flow_launch(vs_field *f, bool rect, int mu, const FlowParams 
     return launch_flow_f18(rect, mu, p, f->stream);
 }
 
-// per-sweep counter pairs in the field's stats buffer
+// per-sweep counter blocks (kSweepSlots each) in the field's stats buffer
 static vs_status ensure_sweep_counts(vs_field *f, int32_t n, const char *who) {
     if (f->sweep_cap >= n) return VS_OK;
     CK(cudaStreamSynchronize(f->stream));
     dev_free(f->ctx, f->sweep_counts);
     dev_free(f->ctx, f->sweep_actions);
-    f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, 2 * sizeof(unsigned long long) * n);
+    f->sweep_counts = (unsigned long long *)dev_alloc(f->ctx, kSweepSlots * sizeof(unsigned long long) * n);
     f->sweep_actions = (double *)dev_alloc(f->ctx, sizeof(double) * n);
     if (!f->sweep_counts || !f->sweep_actions) {
         f->sweep_cap = 0;
@@ -763,8 +794,7 @@ extern "C" vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, 
     vs_status st;
     if (stats) {
         if ((st = ensure_sweep_counts(f, n_sweeps, "vs_smooth_ape"))) return st;
-        if (n_sweeps > 0)
-            CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_sweeps, f->stream));
+        CK(init_sweep_counters(f->sweep_counts, n_sweeps, f->stream));
     }
     if (schedule == VS_SIMULTANEOUS && (st = ensure_scratch(f, field_bytes(f)))) return st;
     ApeParams a;
@@ -783,7 +813,7 @@ extern "C" vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, 
     void *cur = f->U, *nxt = f->scratch;   // simultaneous: alternating buffers, as in vs_smooth
     for (int s = 0; s < n_sweeps; ++s) {
         NvtxRange range("vs APE/UCP sweep");
-        a.counters = stats ? f->sweep_counts + 2 * s : nullptr;
+        a.counters = stats ? f->sweep_counts + kSweepSlots * s : nullptr;
         if (schedule == VS_ANNEALED) {
             a.U = f->U;
             a.Usrc = f->U;
@@ -808,16 +838,17 @@ extern "C" vs_status vs_smooth_ape(vs_field *f, int32_t n_sweeps, double alpha, 
     if (cur != f->U) CK(cudaMemcpyAsync(f->U, cur, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
     f->sweeps_done += n_sweeps;
     if (!stats) return VS_OK;
-    std::vector<unsigned long long> cnt(2 * (size_t)n_sweeps);
+    std::vector<unsigned long long> cnt(kSweepSlots * (size_t)n_sweeps);
     if (n_sweeps > 0)
         CK(cudaMemcpyAsync(cnt.data(), f->sweep_counts, cnt.size() * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, f->stream));
     CK(cudaStreamSynchronize(f->stream));
     for (int s = 0; s < n_sweeps; ++s) {
         memset(&stats[s], 0, sizeof stats[s]);
-        stats[s].n_reject = (int64_t)cnt[2 * s];
+        stats[s].n_reject = (int64_t)cnt[kSweepSlots * s + kCntReject];
         stats[s].n_accept = 4ll * f->g.V - stats[s].n_reject;
-        stats[s].n_singular = (int32_t)cnt[2 * s + 1];
+        stats[s].n_singular = (int32_t)cnt[kSweepSlots * s + kCntSecond];
+        fill_vp_stats(stats[s], &cnt[kSweepSlots * s]);
     }
     return check_device_error(f);
 }
@@ -843,8 +874,7 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
     }
     if (stats) {
         if ((st = ensure_sweep_counts(f, n_steps, "vs_flow_rk3"))) return st;
-        if (n_steps > 0)
-            CK(cudaMemsetAsync(f->sweep_counts, 0, 2 * sizeof(unsigned long long) * n_steps, f->stream));
+        CK(init_sweep_counters(f->sweep_counts, n_steps, f->stream));
     }
     // Luscher's third-order scheme in the low-storage form: stage k uses
     // H_S <- a_k H_Z + b_k H_S and W <- exp(i c_k H_S) W with
@@ -870,7 +900,7 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
     void *cur = f->U, *nxt = f->scratch;
     for (int s = 0; s < n_steps; ++s) {
         NvtxRange range("vs RK3 step");
-        p.counters = stats ? f->sweep_counts + 2 * s : nullptr;
+        p.counters = stats ? f->sweep_counts + kSweepSlots * s : nullptr;
         for (int k = 0; k < 3; ++k) {
             p.a = A[k];
             p.b = B[k];
@@ -889,7 +919,7 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
     if (cur != f->U) CK(cudaMemcpyAsync(f->U, cur, field_bytes(f), cudaMemcpyDeviceToDevice, f->stream));
     f->sweeps_done += n_steps;
     if (!stats) return VS_OK;
-    std::vector<unsigned long long> cnt(2 * (size_t)n_steps);
+    std::vector<unsigned long long> cnt(kSweepSlots * (size_t)n_steps);
     if (n_steps > 0)
         CK(cudaMemcpyAsync(cnt.data(), f->sweep_counts, cnt.size() * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, f->stream));
@@ -897,7 +927,10 @@ extern "C" vs_status vs_flow_rk3(vs_field *f, int32_t n_steps, double step, doub
     for (int s = 0; s < n_steps; ++s) {
         memset(&stats[s], 0, sizeof stats[s]);
         stats[s].n_accept = 4ll * f->g.V;
-        stats[s].n_fp64_exp = (int64_t)cnt[2 * s + 1];
+        stats[s].n_fp64_exp = (int64_t)cnt[kSweepSlots * s + kCntSecond];
+        stats[s].n_label_diff = -1;
+        stats[s].n_undecidable = -1;
+        stats[s].min_margin = std::nan("");
     }
     return check_device_error(f);
 }
@@ -946,6 +979,32 @@ extern "C" vs_status vs_observables(vs_field *f, vs_observables_out *out, double
     out->mean_S = h[0];
     out->mean_SR = h[1];
     out->Q = h[2];
+    return VS_OK;
+}
+
+extern "C" vs_status vs_correlation(vs_field *f, const double *a, const double *b, int32_t where, double *C) {
+    if (!f || !a || !b || !C) return fail(VS_EINVAL, "vs_correlation: NULL argument");
+    if (where != VS_HOST && where != VS_DEVICE) return fail(VS_EINVAL, "vs_correlation: bad `where`");
+    CK(cudaSetDevice(f->ctx->opt.device));
+    const size_t V = f->g.V;
+    const double *da = a, *db = b;
+    if (where == VS_HOST) {
+        vs_status st = ensure_scratch(f, 2 * V * sizeof(double));
+        if (st) return st;
+        double *sc = (double *)f->scratch;
+        CK(cudaMemcpyAsync(sc, a, V * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+        CK(cudaMemcpyAsync(sc + V, b, V * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+        da = sc;
+        db = sc + V;
+    }
+    // 3 x 400 partials, then the result and the three sums
+    double *res = f->partials + 1200;
+    CK(launch_correlation(da, db, (long long)V, f->partials, res, f->stream));
+    double h[4];
+    CK(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    if (!(h[2] > 0) || !(h[3] > 0)) return fail(VS_EINVAL, "vs_correlation: a density is zero on every site");
+    *C = h[0];
     return VS_OK;
 }
 

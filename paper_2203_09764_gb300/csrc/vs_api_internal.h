@@ -45,6 +45,7 @@ struct vs_field {
     double *partials = nullptr;
     double *d_result = nullptr;
     unsigned long long *d_counts = nullptr;
+    unsigned long long *d_sweep = nullptr;  // kSweepSlots counters of vs_subsweep and served jobs
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     void *flowS = nullptr;          // Runge-Kutta exponent H_S, 9 reals per link
@@ -79,10 +80,14 @@ uint64_t field_footprint(const int32_t dims[4], int32_t precision, int32_t stora
 
 // Enqueue n_sweeps on the field's stream.  want_stats: per-sweep counters and
 // actions into the field's stats buffers.  fixed_counters (optional): every
-// sweep adds its reject / FP64 counts into this one pair instead.
+// sweep adds its counts into this one block of kSweepSlots instead.
 vs_status smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double eps, double u0,
                          const vs_anneal *sched, int32_t vp, bool want_stats,
                          unsigned long long *fixed_counters = nullptr);
+
+// Reset n blocks of kSweepSlots counters (stride kSweepSlots): counts to 0, the
+// margin slot to kMarginInit.
+cudaError_t init_sweep_counters(unsigned long long *c, int n, cudaStream_t st);
 
 void serve_shutdown(vs_ctx *c);
 

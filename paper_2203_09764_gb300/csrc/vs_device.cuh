@@ -406,6 +406,30 @@ __device__ __forceinline__ int z3_label(T a, T b) {
     return a < T(0) ? 1 : 0;
 }
 
+// Distance of the trace t = a + ib from the nearest edge of the sector of its
+// label lab, in trace units (|t| times the sine of the angle to that edge).
+// Sector 0 is bounded by the rays at arg = +-pi/3, at distance
+// (sqrt3 a - |b|)/2; the sectors +-1 by the ray at +-pi/3, at distance
+// (|b| - sqrt3 a)/2, and the ray at pi, at distance |b|.  The nearest edge is
+// never more than pi/3 away, so the smaller sine belongs to it.  Errors of
+// the trace are absolute (entries of unit modulus), so this is the quantity
+// a rounding error is measured against.
+template <class T>
+__device__ __forceinline__ T edge_distance(T a, T b, int lab) {
+    const T s = b < T(0) ? -b : b;
+    const T r3a = T(1.7320508075688772) * a;
+    const T d = lab == 0 ? T(0.5) * (r3a - s) : fmin(T(0.5) * (s - r3a), s);
+    return d > T(0) ? d : T(0);
+}
+
+// sin of the angular margin of t from the nearest sector edge (0 for t = 0):
+// monotone in the margin, which is asin of it
+template <class T>
+__device__ __forceinline__ T edge_sine(T a, T b, T d) {
+    const T n2 = a * a + b * b;
+    return n2 > T(0) ? d * rsqrt(n2) : T(0);
+}
+
 // Trace seen by the vortex-preservation test (Sec. VI): Tr U for the original
 // gauge (G == nullptr); after a random gauge transformation G,
 // Tr[G^dag(x) U G(x+mu)] = sum_jk U_jk (G(x+mu) G^dag(x))_kj.  G is stored as

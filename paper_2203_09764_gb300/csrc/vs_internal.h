@@ -19,8 +19,23 @@ struct SubsweepParams {
     double rho, c0, c1;
     float rho_f, c0_f, c1_f;   // the same, rounded once on the host for the FP32 kernels
     int vp;
-    unsigned long long *counters;  // [0] rejects, [1] FP64 exponentials (may be null)
+    unsigned long long *counters;  // kSweepSlots counters of the sweep (kCnt*), or null
 };
+
+// Counter slots of one sweep, filled by the colour-class kernels of the
+// stout, AUS and APE/UCP smoothers (the Runge-Kutta flow uses the second
+// only).  kCntMarginSine holds the smallest sine of a candidate's angular
+// margin from a sector edge as the bits of a non-negative double; it starts
+// at kMarginInit (above any sine).
+enum {
+    kCntReject = 0,       // vortex-preservation rejections
+    kCntSecond = 1,       // FP32: FP64 exponential coefficients; APE: singular blocked matrices
+    kCntLabelDiff = 2,    // candidates whose Z(3) label differs from the reference
+    kCntUndecidable = 3,  // candidates whose trace lies within the precision's error band of an edge
+    kCntMarginSine = 4,
+    kSweepSlots = 8
+};
+constexpr unsigned long long kMarginInit = 0x7f7f7f7f7f7f7f7full;   // a double of about 1.4e306
 
 // process-wide count of direct kernel launches
 void count_launches(int n);
@@ -112,11 +127,17 @@ cudaError_t launch_action(int prec, int nc, const Geo &g, const void *U, double 
 // optional per-site densities in lexicographic order
 cudaError_t launch_observables(int prec, int nc, const Geo &g, const void *U, double *partials, double *out,
                                double *S_site, double *SR_site, double *q_site, cudaStream_t st);
+// C = <a b> / sqrt(<a^2> <b^2>) of two device densities of n values into out[0]
+// (out[1..3]: the sums of a b, a^2, b^2); partials: 3 x 400 doubles
+cudaError_t launch_correlation(const double *a, const double *b, long long n, double *partials, double *out,
+                               cudaStream_t st);
 // counts[0] label diffs, counts[1] charge diffs, counts[2] near-boundary links;
 // margin_bits: min angular margin as the bit pattern of a non-negative double
 cudaError_t launch_vortex(int prec, int nc, const Geo &g, const void *U, const int8_t *ref,
                           int8_t *cur, unsigned long long *counts,
                           unsigned long long *margin_bits, cudaStream_t st, const void *G = nullptr);
+// load the vortex-check kernels now (a first launch would, with lazy loading)
+cudaError_t preload_vortex_kernels();
 cudaError_t launch_reunit(int prec, int nc, const Geo &g, void *U, const int8_t *ref, cudaStream_t st,
                           const void *G = nullptr);
 // random gauge transformation: store G (FP64 host layout [V][3][3][2], on the

@@ -365,6 +365,52 @@ __global__ void k_sum_partials(const double *__restrict__ partials, int n, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Correlation of two densities, Sec. VII Eq. (correlation_s):
+//   C = <a b> / (sqrt<a^2> sqrt<b^2>)
+// three FP64 sums in a fixed order (grid-stride loop over a fixed grid, block
+// tree, then one block over the partials), so the result is bit-reproducible.
+// ---------------------------------------------------------------------------
+
+constexpr int kCorrGrid = 400;
+
+__global__ void __launch_bounds__(kThreads) k_correlation(const double *__restrict__ a, const double *__restrict__ b,
+                                                          long long n, double *partials) {
+    double sab = 0, saa = 0, sbb = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double x = a[i], y = b[i];
+        sab = fma(x, y, sab);
+        saa = fma(x, x, saa);
+        sbb = fma(y, y, sbb);
+    }
+    sab = block_sum(sab);
+    saa = block_sum(saa);
+    sbb = block_sum(sbb);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x] = sab;
+        partials[3 * blockIdx.x + 1] = saa;
+        partials[3 * blockIdx.x + 2] = sbb;
+    }
+}
+
+// out[0] = C, out[1..3] = the three sums (a zero norm leaves C = NaN)
+__global__ void k_correlation_finish(const double *__restrict__ partials, int nb, double *out) {
+    double s[3];
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partials[3 * i + c];
+        s[c] = block_sum(acc);
+    }
+    if (threadIdx.x == 0) {
+        out[1] = s[0];
+        out[2] = s[1];
+        out[3] = s[2];
+        // the means' 1/n cancels between numerator and denominator
+        out[0] = (s[1] > 0 && s[2] > 0) ? s[0] / (sqrt(s[1]) * sqrt(s[2])) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Vortex check
 // ---------------------------------------------------------------------------
 
@@ -750,6 +796,24 @@ cudaError_t launch_observables(int prec, int nc, const Geo &g, const void *U, do
     k_sum_partials3<<<1, 1024, 0, st>>>(partials, b, 1.0 / (double)g.V, out);
     count_launches(2);
     return cudaGetLastError();
+}
+
+cudaError_t launch_correlation(const double *a, const double *b, long long n, double *partials, double *out,
+                               cudaStream_t st) {
+    const int nb = (int)std::min<long long>(nblocks(n), kCorrGrid);
+    k_correlation<<<nb, kThreads, 0, st>>>(a, b, n, partials);
+    k_correlation_finish<<<1, 1024, 0, st>>>(partials, nb, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t preload_vortex_kernels() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_vortex_links<double, 18>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_vortex_links<float, 18>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_vortex_links<float, 12>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_vortex_charges);
+    return e;
 }
 
 cudaError_t launch_vortex(int prec, int nc, const Geo &g, const void *U, const int8_t *ref, int8_t *cur,

@@ -1,14 +1,17 @@
-// vs_noalloc.cu -- vortex check without any allocation.
+// vs_noalloc.cu -- vortex check without device allocation.
 //
 // vs_vortex_check needs scratch memory (a plane of current labels and a few
 // counters), which a field allocates when it is created.  This entry point
 // runs the same two kernels on buffers the caller already owns and keeps the
-// scratch in a fixed, file-scope device array instead, so it never calls
-// cudaMalloc, cudaFree or an allocating library routine.  It also makes no
+// scratch in a fixed, file-scope device array instead, so it never allocates
+// device memory: no cudaMalloc, cudaFree or allocating library routine.  The
+// one allocation it ever makes is on the host: a 64-byte pinned, mapped block
+// per device, made once by vs_noalloc_prepare (which vs_create calls for its
+// device) or else by the first call on that device.  It also makes no
 // synchronising CUDA call, so it stays usable while another stream of the
 // thread captures a graph in the global capture mode: a last one-thread
-// kernel publishes the counters and a sequence number into a small mapped
-// host block, and the host waits for that number (with a time limit).
+// kernel publishes the counters and a sequence number into the mapped host
+// block, and the host waits for that number (with a time limit).
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -49,26 +52,46 @@ struct DeviceScratch {
     volatile unsigned long long *host = nullptr;   // mapped pinned block: 4 report words + sequence
     unsigned long long *host_dev = nullptr;        // its device address
     unsigned long long seq = 0;
+    // sequence number of a call that gave up waiting: its kernels may still
+    // use the scratch, so calls are refused until its result is published
+    unsigned long long stale = 0;
 };
 DeviceScratch g_dev[kMaxDevices];
 
-// First call on a device: the device addresses of the scratch arrays (host
-// code cannot use the arrays' names as device pointers) and the mapped host
-// block.  Called with the device's mutex held.
+// Once per device, with that device current: the device addresses of the
+// scratch arrays (host code cannot use the arrays' names as device
+// pointers), the mapped host block, and the kernels this file launches
+// loaded now (with lazy module loading a first launch loads them).  The
+// thread's capture mode is relaxed meanwhile, so that a first call made
+// while another stream of the thread captures a graph neither fails nor
+// invalidates that capture.  Called with the device's mutex held.
 vs_status setup(DeviceScratch &d) {
     if (d.ready) return VS_OK;
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    cudaError_t e = cudaThreadExchangeStreamCaptureMode(&mode);
+    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaThreadExchangeStreamCaptureMode");
     void *pl = nullptr, *pc = nullptr, *ph = nullptr, *phd = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&pl, g_noalloc_labels);
-    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetSymbolAddress(labels)");
-    e = cudaGetSymbolAddress(&pc, g_noalloc_counts);
-    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetSymbolAddress(counters)");
-    e = cudaHostAlloc(&ph, 8 * sizeof(unsigned long long), cudaHostAllocMapped | cudaHostAllocPortable);
-    if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaHostAlloc");
-    e = cudaHostGetDevicePointer(&phd, ph, 0);
-    if (e != cudaSuccess) {
-        cudaFreeHost(ph);
-        return cuda_fail(e, "vs_vortex_check_noalloc: cudaHostGetDevicePointer");
+    const char *what = "cudaGetSymbolAddress";
+    e = cudaGetSymbolAddress(&pl, g_noalloc_labels);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&pc, g_noalloc_counts);
+    if (e == cudaSuccess) {
+        cudaFuncAttributes fa;
+        what = "kernel loading";
+        e = cudaFuncGetAttributes(&fa, k_noalloc_publish);
+        if (e == cudaSuccess) e = preload_vortex_kernels();
     }
+    if (e == cudaSuccess) {
+        what = "cudaHostAlloc";
+        e = cudaHostAlloc(&ph, 8 * sizeof(unsigned long long), cudaHostAllocMapped | cudaHostAllocPortable);
+    }
+    if (e == cudaSuccess) {
+        what = "cudaHostGetDevicePointer";
+        e = cudaHostGetDevicePointer(&phd, ph, 0);
+        if (e != cudaSuccess) cudaFreeHost(ph);
+    }
+    cudaStreamCaptureMode back = mode;
+    cudaThreadExchangeStreamCaptureMode(&back);
+    if (e != cudaSuccess) return cuda_fail(e, what);
     memset(ph, 0, 8 * sizeof(unsigned long long));
     d.labels = static_cast<int8_t *>(pl);
     d.counts = static_cast<unsigned long long *>(pc);
@@ -80,7 +103,23 @@ vs_status setup(DeviceScratch &d) {
 
 }  // namespace
 
-extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *ref_labels,
+extern "C" vs_status vs_noalloc_prepare(int32_t device) {
+    if (device < 0 || device >= kMaxDevices)
+        return fail(VS_EUNSUPPORTED, "vs_noalloc_prepare: device %d beyond %d", device, kMaxDevices);
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "vs_noalloc_prepare: cudaGetDevice");
+    if (cur != device && (e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "vs_noalloc_prepare");
+    vs_status st;
+    {
+        std::lock_guard<std::mutex> lock(g_dev[device].mu);
+        st = setup(g_dev[device]);
+    }
+    if (cur != device) cudaSetDevice(cur);
+    return st;
+}
+
+extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *ref_labels, const void *gauge,
                                              const int32_t dims[4], int32_t precision,
                                              int32_t storage, void *stream, vs_vortex_report *out) {
     if (!links || !ref_labels || !dims || !out)
@@ -111,6 +150,13 @@ extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *re
     std::lock_guard<std::mutex> lock(d.mu);
     vs_status st = setup(d);
     if (st) return st;
+    if (d.stale) {
+        if (d.host[4] != d.stale)
+            return fail(VS_EBUSY,
+                        "vs_vortex_check_noalloc: an earlier call on device %d gave up waiting and its kernels "
+                        "have not finished; the shared scratch stays in use until they do", dev);
+        d.stale = 0;
+    }
     Geo g;
     for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
     g.Q = dims[0] / 4;
@@ -125,7 +171,7 @@ extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *re
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt + 3, 0x7f, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
         e = launch_vortex(precision == VS_FP32, storage == VS_LINK12 ? 12 : 18, g, links, ref_labels, d.labels,
-                          cnt, cnt + 3, s);
+                          cnt, cnt + 3, s, gauge);
     if (e == cudaSuccess) {
         k_noalloc_publish<<<1, 32, 0, s>>>(cnt, d.host_dev, seq);
         count_launches(1);
@@ -137,8 +183,10 @@ extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *re
     for (long n = 0; d.host[4] != seq; ++n) {
         if (n > 1000) std::this_thread::sleep_for(std::chrono::microseconds(20));
         if ((n & 255) == 0 &&
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > kWaitLimitMs)
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > kWaitLimitMs) {
+            d.stale = seq;
             return fail(VS_EDEVICE, "vs_vortex_check_noalloc: no result from the GPU after %.0f ms", kWaitLimitMs);
+        }
     }
     std::atomic_thread_fence(std::memory_order_acquire);
     unsigned long long h[4];

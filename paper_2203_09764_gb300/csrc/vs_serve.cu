@@ -136,7 +136,7 @@ bool Serve::admit_one(std::unique_lock<std::mutex> &lk) {
         if (st == VS_OK && jp->spec.omega >= 0)
             st = vs_centrifuge(jp->f, jp->spec.omega, jp->spec.centrifuge_seed);
         if (st == VS_OK)
-            if (cudaMemsetAsync(jp->f->d_counts, 0, 8 * sizeof(unsigned long long), jp->stream) != cudaSuccess)
+            if (init_sweep_counters(jp->f->d_sweep, 1, jp->stream) != cudaSuccess)
                 st = fail(VS_EDEVICE, "counter reset failed");
         lk.lock();
         if (st != VS_OK) finish(*jp, st);
@@ -242,7 +242,7 @@ void Serve::step_running(std::unique_lock<std::mutex> &lk, bool &progressed) {
             if (j.inflight.size() < 2) {
                 cudaEvent_t ev = get_event();
                 lk.unlock();
-                vs_status st = enqueue_chunk(j, j.f->d_counts);
+                vs_status st = enqueue_chunk(j, j.f->d_sweep);
                 if (st == VS_OK && cudaEventRecord(ev, j.stream) != cudaSuccess)
                     st = fail(VS_EDEVICE, "event record failed");
                 lk.lock();
@@ -261,7 +261,7 @@ void Serve::step_running(std::unique_lock<std::mutex> &lk, bool &progressed) {
         lk.unlock();
         vs_status st = VS_OK;
         unsigned long long cnt[2] = {0, 0};
-        if (cudaMemcpyAsync(cnt, j.f->d_counts, sizeof cnt, cudaMemcpyDeviceToHost, j.stream) != cudaSuccess ||
+        if (cudaMemcpyAsync(cnt, j.f->d_sweep, sizeof cnt, cudaMemcpyDeviceToHost, j.stream) != cudaSuccess ||
             cudaStreamSynchronize(j.stream) != cudaSuccess)
             st = fail(VS_EDEVICE, "job counters read failed");
         double S = 0;

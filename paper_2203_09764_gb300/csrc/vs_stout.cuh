@@ -322,37 +322,83 @@ __device__ __forceinline__ M3<T> stout_candidate(const M3<T> &sig, const M3<T> &
 #define VS_SUBSWEEP_MINB (512 / VS_SUBSWEEP_THREADS)
 #endif
 
+// Outcome of one link update, for the per-sweep counters.
+template <class T>
+struct Update {
+    bool reject = false;   // the vortex-preservation test refused the candidate
+    bool second = false;   // FP64 exponential coefficients (APE: a singular blocked matrix)
+    bool labdiff = false;  // the candidate's label differs from the reference label
+    bool undec = false;    // the candidate's trace lies within the precision's error band of a sector edge
+    T sine = T(2);         // sine of the candidate's angular margin from a sector edge (2: no candidate)
+};
+
+// Error band of a candidate's trace, in trace units (the entries have unit
+// modulus, so trace errors are absolute).  FP32: one sweep from a common FP64
+// state puts an FP32 candidate within 1.7e-7 per entry of the FP64 one
+// (measured along a 200-sweep trajectory), its trace within ~5e-7; within
+// 2e-6 of an edge the rounding of the FP32 links and arithmetic can decide the
+// vortex-preservation test, so such a candidate is counted as undecidable.
+// FP64: two FP64 implementations differ by ~1e-15 per sweep.
+template <class T> struct EdgeBand;
+template <> struct EdgeBand<float> { static __device__ __forceinline__ float v() { return 2e-6f; } };
+template <> struct EdgeBand<double> { static __device__ __forceinline__ double v() { return 1e-12; } };
+
+// The candidate's label against the reference (Sec. VI), its distance from
+// the nearest sector edge (Sec. I Eq. centre_element) and the margin sine.
+template <class T>
+__device__ __forceinline__ void vp_decide(bool vp, bool want_sine, int ref, T tr_re, T tr_im, Update<T> &u) {
+    const int lab = z3_label<T>(tr_re, tr_im);
+    const T dist = edge_distance<T>(tr_re, tr_im, lab);
+    u.reject = vp && lab != ref;
+    u.labdiff = lab != ref;
+    u.undec = dist < EdgeBand<T>::v();
+    if (want_sine) u.sine = edge_sine<T>(tr_re, tr_im, dist);
+}
+
 // Stout candidate for link (x, MU) at plane position i from its staple sum,
 // vortex-preservation test against the reference label, store if accepted.
 template <class T, int NC, int MU>
 __device__ __forceinline__ void stout_store(const SubsweepParams &a, const Pt &x, int i, const M3<T> &sig,
-                                            const M3<T> &Ux, bool &reject, bool &used64) {
+                                            const M3<T> &Ux, Update<T> &u) {
     const Geo &g = a.g;
     const T rho = sizeof(T) == 4 ? T(a.rho_f) : T(a.rho);
-    M3<T> Un = stout_candidate<T>(sig, Ux, rho, used64);
+    M3<T> Un = stout_candidate<T>(sig, Ux, rho, u.second);
     // 12-real storage keeps rows 0-1 and rebuilds row 2 on every load: the
     // test must see that matrix, not the one computed here
     if (NC == 12) rebuild_row2(Un);
-    if (a.vp) {
-        T tr_re, tr_im;
-        vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re, tr_im);
-        reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
-    }
+    T tr_re, tr_im;
+    vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re, tr_im);
+    vp_decide<T>(a.vp, a.counters != nullptr, (int)a.ref[(long long)MU * g.P + i], tr_re, tr_im, u);
     // a rejected link keeps its value: nothing to write in place (annealed),
     // the old link into the destination when that is another buffer
-    if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Un);
+    if (!u.reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Un);
     else if (a.U != a.Usrc) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Ux);
 }
 
-// per-warp reject and FP64-exponential counts
-__device__ __forceinline__ void count_update(const SubsweepParams &a, bool reject, bool used64) {
-    if (a.counters) {
-        unsigned rb = __ballot_sync(0xffffffffu, reject);
-        unsigned fb = __ballot_sync(0xffffffffu, used64);
-        if ((threadIdx.x & 31) == 0) {
-            if (rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
-            if (fb) atomicAdd(&a.counters[1], (unsigned long long)__popc(fb));
-        }
+// Per-warp counts into a sweep's counter slots (kCnt* in vs_internal.h):
+// rejects, the second count (FP64 exponentials; singular blocked matrices in
+// APE), label differences, undecidable candidates, and the smallest margin
+// sine (as the bits of a non-negative double, whose order is that of
+// unsigned integers).
+template <class T>
+__device__ __forceinline__ void count_update(unsigned long long *c, const Update<T> &u) {
+    if (!c) return;
+    const unsigned rb = __ballot_sync(0xffffffffu, u.reject);
+    const unsigned fb = __ballot_sync(0xffffffffu, u.second);
+    const unsigned lb = __ballot_sync(0xffffffffu, u.labdiff);
+    const unsigned ub = __ballot_sync(0xffffffffu, u.undec);
+    T m = u.sine;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v < m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (rb) atomicAdd(&c[kCntReject], (unsigned long long)__popc(rb));
+        if (fb) atomicAdd(&c[kCntSecond], (unsigned long long)__popc(fb));
+        if (lb) atomicAdd(&c[kCntLabelDiff], (unsigned long long)__popc(lb));
+        if (ub) atomicAdd(&c[kCntUndecidable], (unsigned long long)__popc(ub));
+        if (m < T(2)) atomicMin(&c[kCntMarginSine], (unsigned long long)__double_as_longlong((double)m));
     }
 }
 
@@ -364,7 +410,7 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     k_subsweep(SubsweepParams a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false, used64 = false;
+    Update<T> u;
     if (active) {
         const Geo &g = a.g;
         Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
@@ -373,9 +419,9 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
         M3<T> sig = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
         M3<T> Ux = load_link<T, NC>(Us, g.P, MU, i);
-        stout_store<T, NC, MU>(a, x, i, sig, Ux, reject, used64);
+        stout_store<T, NC, MU>(a, x, i, sig, Ux, u);
     }
-    count_update(a, reject, used64);
+    count_update<T>(a.counters, u);
 }
 
 // ---------------------------------------------------------------------------
@@ -763,7 +809,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, 4) k_subsweep_pring(SubsweepP
     float2 *ring2 = reinterpret_cast<float2 *>(pring_dyn + 6 * (NC / 4) * VS_RING_THREADS);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false, used64 = false;
+    Update<float> u;
     if (active) {
         const Geo &g = a.g;
         Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
@@ -772,9 +818,9 @@ __global__ void __launch_bounds__(VS_RING_THREADS, 4) k_subsweep_pring(SubsweepP
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         const M3<float> sig = staple_sum_plain_ring<NC, MU>(g, Us, x, a.c0_f, R);
         const M3<float> Ux = load_link<float, NC>(Us, g.P, MU, i);
-        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
+        stout_store<float, NC, MU>(a, x, i, sig, Ux, u);
     }
-    count_update(a, reject, used64);
+    count_update<float>(a.counters, u);
 }
 
 template <int NC, int MU>
@@ -784,7 +830,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_fuse
     float2 *ring2 = reinterpret_cast<float2 *>(ring6_dyn + 6 * (NC / 4) * VS_RING_THREADS);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false, used64 = false;
+    Update<float> u;
     if (active) {
         const Geo &g = a.g;
         Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
@@ -792,9 +838,9 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_fuse
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
         M3<float> sig = staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.Usrc), x, a.c0_f, a.c1_f, R, Ux);
-        stout_store<float, NC, MU>(a, x, i, sig, Ux, reject, used64);
+        stout_store<float, NC, MU>(a, x, i, sig, Ux, u);
     }
-    count_update(a, reject, used64);
+    count_update<float>(a.counters, u);
 }
 
 }  // namespace vs
@@ -860,7 +906,7 @@ __device__ __forceinline__ void maxretr(M3<T> &u, const M3<T> &Vb, int n_hits) {
 // vortex-preservation test, store if accepted.
 template <class T, int NC, int MU>
 __device__ __forceinline__ void aus_finish(const AusParams &a, const Pt &x, int i, M3<T> Vb, M3<T> u,
-                                           bool &reject) {
+                                           Update<T> &up) {
     const Geo &g = a.g;
     const T al = sizeof(T) == 4 ? T(a.alpha_f) : T(a.alpha);
     const T w6 = al / T(6), w1 = T(1) - al;
@@ -871,12 +917,10 @@ __device__ __forceinline__ void aus_finish(const AusParams &a, const Pt &x, int 
     }
     maxretr<T>(u, Vb, a.n_hits);
     if (NC == 12) rebuild_row2(u);
-    if (a.vp) {
-        T tr_re, tr_im;
-        vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, u, tr_re, tr_im);
-        reject = z3_label<T>(tr_re, tr_im) != (int)a.ref[(long long)MU * g.P + i];
-    }
-    if (!reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, u);
+    T tr_re, tr_im;
+    vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, u, tr_re, tr_im);
+    vp_decide<T>(a.vp, a.counters != nullptr, (int)a.ref[(long long)MU * g.P + i], tr_re, tr_im, up);
+    if (!up.reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, u);
 }
 
 template <class T, int NC, bool RECT, int MU>
@@ -884,7 +928,7 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     k_aus(AusParams a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false;
+    Update<T> up;
     if (active) {
         const Geo &g = a.g;
         const Pt x = class_site<MU>(g, a.colour, t);
@@ -893,12 +937,9 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
         const M3<T> Vb = staple_sum<T, NC, RECT, MU>(g, U, x, c0, c1);
         const M3<T> u = load_link<T, NC>(U, g.P, MU, i);
-        aus_finish<T, NC, MU>(a, x, i, Vb, u, reject);
+        aus_finish<T, NC, MU>(a, x, i, Vb, u, up);
     }
-    if (a.counters) {
-        unsigned rb = __ballot_sync(0xffffffffu, reject);
-        if ((threadIdx.x & 31) == 0 && rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
-    }
+    count_update<T>(a.counters, up);
 }
 
 // FP32 over-improved AUS with the one-pass link stream of k_subsweep_fused.
@@ -909,7 +950,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_aus_ring(AusP
     float2 *ring2 = reinterpret_cast<float2 *>(aus_dyn + 6 * (NC / 4) * VS_RING_THREADS);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false;
+    Update<float> up;
     if (active) {
         const Geo &g = a.g;
         const Pt x = class_site<MU>(g, a.colour, t);
@@ -917,12 +958,9 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_aus_ring(AusP
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
         const M3<float> Vb = staple_sum_fused<NC, MU>(g, static_cast<const float *>(a.U), x, a.c0_f, a.c1_f, R, Ux);
-        aus_finish<float, NC, MU>(a, x, i, Vb, Ux, reject);
+        aus_finish<float, NC, MU>(a, x, i, Vb, Ux, up);
     }
-    if (a.counters) {
-        unsigned rb = __ballot_sync(0xffffffffu, reject);
-        if ((threadIdx.x & 31) == 0 && rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
-    }
+    count_update<float>(a.counters, up);
 }
 
 // FP32 AUS + MaxReTr with plaquette staples (eps = 1; alpha = 1 is cooling)
@@ -934,7 +972,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, 4) k_aus_pring(AusParams a) {
     float2 *ring2 = reinterpret_cast<float2 *>(ausp_dyn + 6 * (NC / 4) * VS_RING_THREADS);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = t < a.n_threads;
-    bool reject = false;
+    Update<float> up;
     if (active) {
         const Geo &g = a.g;
         const Pt x = class_site<MU>(g, a.colour, t);
@@ -943,12 +981,9 @@ __global__ void __launch_bounds__(VS_RING_THREADS, 4) k_aus_pring(AusParams a) {
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         const M3<float> Vb = staple_sum_plain_ring<NC, MU>(g, Us, x, a.c0_f, R);
         const M3<float> Ux = load_link<float, NC>(Us, g.P, MU, i);
-        aus_finish<float, NC, MU>(a, x, i, Vb, Ux, reject);
+        aus_finish<float, NC, MU>(a, x, i, Vb, Ux, up);
     }
-    if (a.counters) {
-        unsigned rb = __ballot_sync(0xffffffffu, reject);
-        if ((threadIdx.x & 31) == 0 && rb) atomicAdd(&a.counters[0], (unsigned long long)__popc(rb));
-    }
+    count_update<float>(a.counters, up);
 }
 
 }  // namespace vs

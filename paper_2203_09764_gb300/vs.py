@@ -50,7 +50,9 @@ class vs_anneal(ctypes.Structure):
 class vs_sweep_stats(ctypes.Structure):
     _fields_ = [("n_accept", ctypes.c_int64), ("n_reject", ctypes.c_int64),
                 ("n_fp64_exp", ctypes.c_int64), ("action", ctypes.c_double),
-                ("has_action", ctypes.c_int32), ("n_singular", ctypes.c_int32)]
+                ("has_action", ctypes.c_int32), ("n_singular", ctypes.c_int32),
+                ("n_label_diff", ctypes.c_int64), ("n_undecidable", ctypes.c_int64),
+                ("min_margin", ctypes.c_double)]
 
 
 class vs_vortex_report(ctypes.Structure):
@@ -68,7 +70,8 @@ class vs_field_desc(ctypes.Structure):
                 ("storage", ctypes.c_int32), ("n_sites", ctypes.c_int64),
                 ("plane_stride", ctypes.c_int64), ("n_components", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("links", ctypes.c_void_p),
-                ("labels", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+                ("labels", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("gauge", ctypes.c_void_p)]
 
 
 class vs_job(ctypes.Structure):
@@ -120,6 +123,7 @@ _SIGS = {
     "vs_vortex_check": (ctypes.c_int32, [P, ctypes.POINTER(vs_vortex_report)]),
     "vs_action": (ctypes.c_int32, [P, ctypes.POINTER(ctypes.c_double)]),
     "vs_observables": (ctypes.c_int32, [P, ctypes.POINTER(vs_observables_out), P, P, P, ctypes.c_int32]),
+    "vs_correlation": (ctypes.c_int32, [P, P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "vs_read_field": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_read_labels": (ctypes.c_int32, [P, P, ctypes.c_int32]),
     "vs_field_count_nonfinite": (ctypes.c_int32, [P, ctypes.POINTER(ctypes.c_int64)]),
@@ -140,8 +144,9 @@ _SIGS = {
     "vs_serve_stats_get": (ctypes.c_int32, [P, ctypes.POINTER(vs_serve_stats)]),
     "vs_now_ms": (ctypes.c_double, [P]),
     "vs_kernel_launches": (ctypes.c_int64, []),
-    "vs_vortex_check_noalloc": (ctypes.c_int32, [P, P, P, ctypes.c_int32, ctypes.c_int32, P,
+    "vs_vortex_check_noalloc": (ctypes.c_int32, [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P,
                                                  ctypes.POINTER(vs_vortex_report)]),
+    "vs_noalloc_prepare": (ctypes.c_int32, [ctypes.c_int32]),
 }
 
 VS_NOALLOC_MAX_LINKS = 8 * 1024 * 1024
@@ -193,16 +198,18 @@ def _host_links(a):
 def _buf(f, a, kind, n_entries, what):
     """(pointer, where) of a buffer the library reads or writes for field f,
     after checking what the C side cannot: the element type (kind "c" for
-    complex128 entries, given as complex128 or as float64 (re, im) pairs, "i8"
-    for labels), contiguity, the byte size (n_entries of 16 or 1 bytes), and
-    for a CUDA tensor the field's device."""
-    nbytes = n_entries * (16 if kind == "c" else 1)
+    complex128 entries, given as complex128 or as float64 (re, im) pairs, "f8"
+    for float64 values, "i8" for labels), contiguity, the byte size (n_entries
+    of 16, 8 or 1 bytes), and for a CUDA tensor the field's device."""
+    nbytes = n_entries * {"c": 16, "f8": 8, "i8": 1}[kind]
     if isinstance(a, np.ndarray):
-        ok = a.dtype in (np.complex128, np.float64) if kind == "c" else a.dtype == np.int8
+        ok = {"c": a.dtype in (np.complex128, np.float64), "f8": a.dtype == np.float64,
+              "i8": a.dtype == np.int8}[kind]
         size, contiguous = a.nbytes, a.flags["C_CONTIGUOUS"]
     elif hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
         import torch
-        ok = a.dtype in (torch.complex128, torch.float64) if kind == "c" else a.dtype == torch.int8
+        ok = {"c": a.dtype in (torch.complex128, torch.float64), "f8": a.dtype == torch.float64,
+              "i8": a.dtype == torch.int8}[kind]
         size, contiguous = a.numel() * a.element_size(), a.is_contiguous()
         if a.is_cuda and a.device.index != vs_field_describe(f)["device"]:
             raise ValueError("%s: tensor on %s, the field is on cuda:%d"
@@ -211,7 +218,8 @@ def _buf(f, a, kind, n_entries, what):
         raise TypeError("%s: expected a numpy array or a torch tensor" % what)
     if not ok:
         raise TypeError("%s: element type %s (expected %s)"
-                        % (what, a.dtype, "complex128 or float64 pairs" if kind == "c" else "int8"))
+                        % (what, a.dtype, {"c": "complex128 or float64 pairs", "f8": "float64",
+                                           "i8": "int8"}[kind]))
     if not contiguous:
         raise ValueError("%s: buffer must be contiguous" % what)
     if size != nbytes:
@@ -347,7 +355,9 @@ def vs_smooth(f, n_sweeps, rho, epsilon=1.0, u0=1.0, kind=VS_ANNEALED, rho_per_s
     if not stats:
         return None
     return [dict(n_accept=s.n_accept, n_reject=s.n_reject, n_fp64_exp=s.n_fp64_exp,
-                 action=(s.action if s.has_action else None)) for s in st[:int(n_sweeps)]]
+                 action=(s.action if s.has_action else None), n_label_diff=s.n_label_diff,
+                 n_undecidable=s.n_undecidable, min_margin=s.min_margin)
+            for s in st[:int(n_sweeps)]]
 
 
 def vs_smooth_aus(f, n_sweeps, alpha, epsilon=-0.25, u0=1.0, n_hits=3, reunit_every=10,
@@ -358,7 +368,8 @@ def vs_smooth_aus(f, n_sweeps, alpha, epsilon=-0.25, u0=1.0, n_hits=3, reunit_ev
                              ctypes.cast(st, ctypes.c_void_p) if stats else None))
     if not stats:
         return None
-    return [dict(n_accept=s.n_accept, n_reject=s.n_reject) for s in st[:int(n_sweeps)]]
+    return [dict(n_accept=s.n_accept, n_reject=s.n_reject, n_label_diff=s.n_label_diff,
+                 n_undecidable=s.n_undecidable, min_margin=s.min_margin) for s in st[:int(n_sweeps)]]
 
 
 def vs_smooth_ape(f, n_sweeps, alpha, epsilon=-0.25, u0=1.0, schedule=None, reunit_every=10,
@@ -372,7 +383,8 @@ def vs_smooth_ape(f, n_sweeps, alpha, epsilon=-0.25, u0=1.0, schedule=None, reun
                              ctypes.cast(st, ctypes.c_void_p) if stats else None))
     if not stats:
         return None
-    return [dict(n_accept=s.n_accept, n_reject=s.n_reject, n_singular=s.n_singular)
+    return [dict(n_accept=s.n_accept, n_reject=s.n_reject, n_singular=s.n_singular,
+                 n_label_diff=s.n_label_diff, n_undecidable=s.n_undecidable, min_margin=s.min_margin)
             for s in st[:int(n_sweeps)]]
 
 
@@ -398,15 +410,23 @@ def vs_vortex_check(f):
                 n_near_boundary=r.n_near_boundary, min_margin=r.min_margin)
 
 
-def vs_vortex_check_noalloc(links, ref_labels, dims, precision, storage, stream=None):
+def vs_vortex_check_noalloc(links, ref_labels, dims, precision, storage, stream=None, gauge=None):
     """The vortex check on caller-owned device buffers (device pointers as
-    integers, e.g. from vs_field_describe), with no allocation; see vs.h."""
+    integers, e.g. from vs_field_describe; gauge: the field's random gauge
+    transformation or None), with no device allocation; see vs.h."""
     r = vs_vortex_report()
     _check(lib.vs_vortex_check_noalloc(ctypes.c_void_p(int(links)), ctypes.c_void_p(int(ref_labels)),
+                                       ctypes.c_void_p(int(gauge)) if gauge else None,
                                        _dims(dims), int(precision), int(storage), _stream(stream),
                                        ctypes.byref(r)))
     return dict(n_links=r.n_links, n_label_diff=r.n_label_diff, n_charge_diff=r.n_charge_diff,
                 n_near_boundary=r.n_near_boundary, min_margin=r.min_margin)
+
+
+def vs_noalloc_prepare(device=0):
+    """The once-per-device set-up of vs_vortex_check_noalloc (vs_create does it
+    for its own device)."""
+    _check(lib.vs_noalloc_prepare(int(device)))
 
 
 def vs_action(f):
@@ -432,11 +452,18 @@ def vs_observables(f, per_site=False):
     return r
 
 
-def correlation(a, b):
-    """C_XY = <a b> / sqrt(<a^2> <b^2>) of two densities (Sec. VII, Eq. correlation_s)."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.mean(a * b) / np.sqrt(np.mean(a * a) * np.mean(b * b)))
+def vs_correlation(f, a, b):
+    """C_XY of two per-site densities over the field's V sites (Sec. VII,
+    Eq. correlation_s), computed by the library: a, b float64 [V] numpy arrays
+    or torch CUDA tensors (both of one kind)."""
+    V = _field_sites(f)
+    pa, wa = _buf(f, a, "f8", V, "vs_correlation a")
+    pb, wb = _buf(f, b, "f8", V, "vs_correlation b")
+    if wa != wb:
+        raise ValueError("vs_correlation: a and b must both be host or both device buffers")
+    C = ctypes.c_double()
+    _check(lib.vs_correlation(f, pa, pb, wa, ctypes.byref(C)))
+    return C.value
 
 
 def _field_sites(f):
@@ -543,7 +570,7 @@ def vs_field_describe(f):
     _check(lib.vs_field_describe(f, ctypes.byref(d)))
     return dict(dims=tuple(d.dims), precision=d.precision, storage=d.storage, n_sites=d.n_sites,
                 plane_stride=d.plane_stride, n_components=d.n_components, device=d.device,
-                links=d.links, labels=d.labels, stream=d.stream)
+                links=d.links, labels=d.labels, stream=d.stream, gauge=d.gauge)
 
 
 def vs_layout_index(dims, x):

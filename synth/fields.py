@@ -52,14 +52,27 @@ def haar_su3(n, seed, offset=0):
     return np.ascontiguousarray(q)
 
 
-def haar_field(dims, seed, chunk=1 << 20):
-    """A hot-start gauge field: every link an independent Haar SU(3) matrix."""
+def haar_field(dims, seed, chunk=1 << 18, workers=None):
+    """A hot-start gauge field: every link an independent Haar SU(3) matrix.
+    Chunks of the counter-mode stream are drawn on a thread pool (numpy's
+    batched QR releases the interpreter lock); the result does not depend on
+    the chunking or the number of threads."""
+    import concurrent.futures as cf
+    import os
     V = lattice_volume(dims)
     n = 4 * V
     out = np.empty((n, 3, 3), dtype=np.complex128)
-    for a in range(0, n, chunk):
+
+    def fill(a):
         b = min(n, a + chunk)
         out[a:b] = haar_su3(b - a, seed, offset=18 * a)
+
+    starts = range(0, n, chunk)
+    if len(starts) == 1:
+        fill(0)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=workers or min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, starts))
     return out.reshape(4, V, 3, 3)
 
 

@@ -11,10 +11,9 @@ import synth
 @functools.lru_cache(maxsize=None)
 def cooled_labels(dims, seed, n_cool=20):
     """The cooled hot-start workload input: Haar SU(3) links from `seed`,
-    n_cool sweeps of oracle MaxReTr cooling, each link projected to Z(3)."""
-    U = synth.haar_field(dims, seed)
-    U = O.cool(dims, U, n_cool)
-    return O.labels(dims, U)
+    n_cool sweeps of oracle MaxReTr cooling, each link projected to Z(3)
+    (built by the oracle, cached on disk)."""
+    return O.cooled_labels(dims, seed, n_cool)
 
 
 def oracle_pipeline(dims, labels, omega, cseed, n_sweeps, rho, eps, vp=True,

@@ -63,8 +63,8 @@ def test_reference_arm_line_on_rank0():
     import json
     env = dict(os.environ, RANK="0", WORLD_SIZE="1", CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True,
-                       text=True, timeout=600)
+                        "--steps", "1", "--warmup", "0", "--lattice", "8,8,8,8"], env=env,
+                       capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -78,3 +78,8 @@ def test_reference_arm_line_on_rank0():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+    # what was timed: ms_per_step is the measured sample (config.sweeps sweeps),
+    # the whole-step figure only under its own, labelled key
+    assert d["config"]["sweeps"] == 1 and d["config"]["lattice"] == [8, 8, 8, 8]
+    assert abs(d["ms_per_step"] - cb["seconds"] * 1e3) < 1e-6 * d["ms_per_step"]
+    assert d["extrapolated_ms_per_workload_step"]["sweeps"] == 300

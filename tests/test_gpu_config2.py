@@ -1,0 +1,89 @@
+"""The 16^3 x 32 workload in full: cooled hot start (seed 2), centrifuge
+(omega = 0.02), then 200 annealed over-improved stout sweeps (eps = -0.25,
+rho = 0.06, u0 = 1) with vortex preservation -- the oracle and the GPU in FP64
+and in FP32 (18-real links, re-unitarised every 10 sweeps), sweep by sweep
+(Sec. II.A Eqs. stout and generator, Sec. III Eq. over-improvement, Sec. V.B
+the annealed Euler flow, Sec. VI the vortex-preservation test).
+
+Asserted: the Z(3) labels and centre charges of both GPU fields equal the
+original ones after the last sweep (bit-exact, Sec. VI), the FP64 GPU run
+tracks the oracle link by link to 1e-10 over the first 20 sweeps (before the
+flow's amplification of rounding differences, ~1.5x per sweep on these
+fields, takes over) with the same rejection counts there, and every sweep's
+action in both precisions stays within 2e-3 relative of the oracle's.
+Recorded (printed as one JSON line): per precision, the largest link and
+relative action differences per sweep and the first sweeps at which they
+exceed 1e-5 and 1e-6.
+"""
+
+import json
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.gpu_common import cooled_labels
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+vs = pytest.importorskip("paper_2203_09764_gb300.vs")
+
+DIMS = (16, 16, 16, 32)
+N_SWEEPS = 200
+RHO, EPS, OMEGA = 0.06, -0.25, 0.02
+
+
+def _first_above(xs, tol):
+    for k, x in enumerate(xs):
+        if x > tol:
+            return k + 1
+    return None
+
+
+def test_full_200_sweep_run_against_the_oracle():
+    lab = cooled_labels(DIMS, 2)
+    U = O.centrifuge(DIMS, lab, OMEGA, 1234)
+    ctx = vs.vs_create(0)
+    fields = {}
+    for name, prec in (("fp64", vs.VS_FP64), ("fp32", vs.VS_FP32)):
+        f = vs.vs_field_create(ctx, DIMS, prec, vs.VS_LINK18)
+        vs.vs_load_field(f, labels=lab)
+        vs.vs_centrifuge(f, OMEGA, 1234)
+        fields[name] = f
+    assert np.abs(vs.vs_read_field(fields["fp64"]) - U).max() < 1e-14
+    rec = {n: {"link": [], "action": [], "rejects_equal": []} for n in fields}
+    for sweep in range(N_SWEEPS):
+        U, rej = O.smooth(DIMS, U, lab, 1, RHO, eps=EPS, vp=True)
+        S = O.action(DIMS, U)
+        for name, f in fields.items():
+            st = vs.vs_smooth(f, 1, RHO, EPS, vortex_preserve=True, reunit_every=10, stats=True)[0]
+            Ug = vs.vs_read_field(f)
+            rec[name]["link"].append(float(np.abs(Ug - U).max()))
+            rec[name]["action"].append(abs(vs.vs_action(f) / S - 1.0))
+            rec[name]["rejects_equal"].append(st["n_reject"] == int(rej[0]))
+    checks = {n: vs.vs_vortex_check(f) for n, f in fields.items()}
+    cur = {n: vs.vs_current_labels(f) for n, f in fields.items()}
+    for f in fields.values():
+        vs.vs_field_destroy(f)
+    vs.vs_destroy(ctx)
+
+    summary = {"lattice": list(DIMS), "sweeps": N_SWEEPS}
+    for name, r in rec.items():
+        summary[name] = {
+            "max_link_diff_at": {str(k): r["link"][k - 1] for k in (1, 10, 20, 50, 100, 150, 200)},
+            "rel_action_diff_at": {str(k): r["action"][k - 1] for k in (1, 10, 20, 50, 100, 150, 200)},
+            "first_sweep_links_above_1e-5": _first_above(r["link"], 1e-5),
+            "first_sweep_action_above_1e-6": _first_above(r["action"], 1e-6),
+            "max_rel_action_diff": max(r["action"]),
+            "sweeps_with_equal_rejections": int(sum(r["rejects_equal"])),
+        }
+    print("CONFIG2 " + json.dumps(summary))
+
+    lab_ch = O.centre_charges(DIMS, lab)
+    for name in fields:
+        assert checks[name]["n_label_diff"] == 0 and checks[name]["n_charge_diff"] == 0
+        assert np.array_equal(cur[name], lab)
+        assert np.array_equal(O.centre_charges(DIMS, cur[name]), lab_ch)
+        assert max(rec[name]["action"]) < 2e-3
+    assert max(rec["fp64"]["link"][:20]) < 1e-10
+    assert all(rec["fp64"]["rejects_equal"][:20])

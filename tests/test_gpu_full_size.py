@@ -62,7 +62,7 @@ def test_sampled_class_update_at_full_size(DIMS, storage, tol, n_sample):
         arg = np.angle(np.trace(cand))
         margin = min(abs(arg - np.pi / 3), abs(arg + np.pi / 3), np.pi - abs(arg))
         if margin < 1e-5:
-            continue                               # within FP32 noise of a sector edge
+            continue                               # within the FP32 error band of a sector edge
         if accept:
             assert np.abs(U1[mu, s] - cand).max() < tol
         else:
@@ -241,18 +241,24 @@ def test_every_link_of_a_periodic_field_at_full_size(path, prec, storage, tol):
     vs.vs_load_field(f, links=_tile(U0))
     assert np.array_equal(_first_tile_if_periodic(vs.vs_read_labels(f)), lab)
     eps, rho, alpha = -0.25, 0.06, 0.02
+    n_undec = None                        # undecidable links the GPU counted (VP paths)
     if path == "stout":
-        vs.vs_smooth(f, 1, rho, eps, vortex_preserve=True, reunit_every=0)
+        st = vs.vs_smooth(f, 1, rho, eps, vortex_preserve=True, reunit_every=0, stats=True)
         Uo, rej = O.smooth(TILE, U0, lab, 1, rho, eps=eps, vp=True)
+        n_undec = st[0]["n_undecidable"]
     elif path == "stout_simultaneous":
-        vs.vs_smooth(f, 1, rho, eps, vortex_preserve=True, reunit_every=0, kind=vs.VS_SIMULTANEOUS)
+        st = vs.vs_smooth(f, 1, rho, eps, vortex_preserve=True, reunit_every=0, kind=vs.VS_SIMULTANEOUS,
+                          stats=True)
         Uo, rej = O.smooth(TILE, U0, lab, 1, rho, eps=eps, vp=True, schedule=O.SIMULTANEOUS)
+        n_undec = st[0]["n_undecidable"]
     elif path == "aus_maxretr":
-        vs.vs_smooth_aus(f, 1, alpha, eps, n_hits=3, reunit_every=0, vortex_preserve=True)
+        st = vs.vs_smooth_aus(f, 1, alpha, eps, n_hits=3, reunit_every=0, vortex_preserve=True, stats=True)
         Uo, rej = O.aus(TILE, U0, lab, 1, alpha, eps=eps, n_hits=3, vp=True)
+        n_undec = st[0]["n_undecidable"]
     elif path == "aus_ucp":
-        vs.vs_smooth_ape(f, 1, alpha, eps, reunit_every=0, vortex_preserve=True)
+        st = vs.vs_smooth_ape(f, 1, alpha, eps, reunit_every=0, vortex_preserve=True, stats=True)
         Uo, rej = O.ape_ucp(TILE, U0, lab, 1, alpha, eps=eps, vp=True)
+        n_undec = st[0]["n_undecidable"]
     elif path == "ape_simultaneous":
         vs.vs_smooth_ape(f, 1, 0.5, eps, schedule=vs.VS_SIMULTANEOUS, reunit_every=0,
                          vortex_preserve=False)
@@ -266,7 +272,12 @@ def test_every_link_of_a_periodic_field_at_full_size(path, prec, storage, tol):
     vs.vs_destroy(ctx)
 
     d, split = _split_links(Ug, Uo, U0, 1e-5 if prec == vs.VS_FP32 else 1e-10)
-    assert int(split.sum()) <= (8 if prec == vs.VS_FP32 else 0)
+    if prec == vs.VS_FP64 or n_undec is None:
+        assert int(split.sum()) == 0
+    else:
+        # decisions equal the oracle's except for links counted undecidable
+        # (each of the 512 copies of the 8^4 tile counts its own)
+        assert int(split.sum()) * int(np.prod(REPS)) <= n_undec
     assert float(d[~split].max()) < tol
     if rej is not None and path != "ape_simultaneous":
         assert int(rej.sum()) > 0                  # the sweep exercises rejections
