@@ -443,6 +443,10 @@ vs_status vs_cancel(vs_ctx *ctx, int64_t ticket);
 typedef struct {
     int64_t submitted, completed, cancelled, running, waiting;
     uint64_t bytes_in_use, peak_bytes_in_use;
+    /* chunk graphs (a job's sweeps are replayed in chunks of reunit_every
+     * sweeps from a captured CUDA graph): instantiated anew, or taken from the
+     * idle graphs of the same shape and updated with the job's pointers */
+    int64_t graphs_instantiated, graphs_reused;
 } vs_serve_stats;
 
 vs_status vs_serve_stats_get(vs_ctx *ctx, vs_serve_stats *out);

@@ -151,25 +151,24 @@ __device__ __forceinline__ f2pk fma2(f2pk a, f2pk b, f2pk c) {
     return d;
 }
 
-// r = c + a * b in FP32: per entry, P = (Re c, Im c) + sum_k Re a_ik (Re b_kj, Im b_kj)
-// and Q = sum_k Im a_ik (Re b_kj, Im b_kj), each a chain of paired FMAs in k
-// order, then r_ij = (P.re - Q.im, P.im + Q.re).  Every entry goes through
-// the same operations, so entries built from equal inputs come out
-// bit-identical (a product of matrices proportional to the identity stays
+// r = c + a * b in FP32: per entry one chain of paired FMAs in k order,
+//   (Re r_ij, Im r_ij) = (Re c, Im c) + sum_k [Re a_ik (Re b_kj, Im b_kj) + Im a_ik (-Im b_kj, Re b_kj)],
+// with the right factor's entries also kept as swapped, negated pairs, so no
+// separate additions combine real and imaginary parts (18 fewer FP32
+// operations per product than two chains and a combine step).  Every entry
+// goes through the same operations, so entries built from equal inputs come
+// out bit-identical (a product of matrices proportional to the identity stays
 // exactly so).
 template <bool ACC>
 __device__ __forceinline__ void m3_mul_f32(M3<float> &r, const M3<float> &a, const M3<float> &b) {
-    f2pk bb[9];
+    f2pk bb[9], bs[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) bb[e] = pk2(b.re[e], b.im[e]);
+    for (int e = 0; e < 9; ++e) { bb[e] = pk2(b.re[e], b.im[e]); bs[e] = pk2(-b.im[e], b.re[e]); }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        f2pk P[3], Q[3];
+        f2pk P[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            P[j] = ACC ? pk2(r.re[i * 3 + j], r.im[i * 3 + j]) : pk2(0.f, 0.f);
-            Q[j] = pk2(0.f, 0.f);
-        }
+        for (int j = 0; j < 3; ++j) P[j] = ACC ? pk2(r.re[i * 3 + j], r.im[i * 3 + j]) : pk2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const f2pk ar = pk2(a.re[i * 3 + k], a.re[i * 3 + k]);
@@ -177,17 +176,11 @@ __device__ __forceinline__ void m3_mul_f32(M3<float> &r, const M3<float> &a, con
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 P[j] = fma2(ar, bb[k * 3 + j], P[j]);
-                Q[j] = fma2(ai, bb[k * 3 + j], Q[j]);
+                P[j] = fma2(ai, bs[k * 3 + j], P[j]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float px, py, qx, qy;
-            upk2(P[j], px, py);
-            upk2(Q[j], qx, qy);
-            r.re[i * 3 + j] = px - qy;
-            r.im[i * 3 + j] = py + qx;
-        }
+        for (int j = 0; j < 3; ++j) upk2(P[j], r.re[i * 3 + j], r.im[i * 3 + j]);
     }
 }
 
@@ -334,16 +327,17 @@ __device__ __forceinline__ void m3_scale(M3<T> &r, T s) {
 //   double, 18 reals: 9 planes of double2 (one complex entry each)
 // A plane holding w reals per site starts at (reals before it) * P and site i
 // sits at w * i inside it, so every load is one aligned 8- or 16-byte vector.
-// row 2 = conj(row 0 x row 1): the third row of an SU(3) matrix from the first two
+// row 2 = conj(row 0 x row 1): the third row of an SU(3) matrix from the first two,
+// each component one chain of fused multiply-adds (four operations)
 template <class T>
 __device__ __forceinline__ void rebuild_row2(M3<T> &m) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-        T cr = m.re[j1] * m.re[3 + j2] - m.im[j1] * m.im[3 + j2]
-             - (m.re[j2] * m.re[3 + j1] - m.im[j2] * m.im[3 + j1]);
-        T ci = m.re[j1] * m.im[3 + j2] + m.im[j1] * m.re[3 + j2]
-             - (m.re[j2] * m.im[3 + j1] + m.im[j2] * m.re[3 + j1]);
+        T cr = fma(m.re[j1], m.re[3 + j2], fma(-m.im[j1], m.im[3 + j2],
+                   fma(-m.re[j2], m.re[3 + j1], m.im[j2] * m.im[3 + j1])));
+        T ci = fma(m.re[j1], m.im[3 + j2], fma(m.im[j1], m.re[3 + j2],
+                   fma(-m.re[j2], m.im[3 + j1], -(m.im[j2] * m.re[3 + j1]))));
         m.re[6 + j] = cr;
         m.im[6 + j] = -ci;
     }

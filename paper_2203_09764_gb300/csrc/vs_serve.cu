@@ -5,7 +5,12 @@
 // of the device footprints of the running jobs stays within the HBM budget.
 // Each running job has its own field and stream; its sweeps are enqueued in
 // chunks (one replay of a CUDA graph holding `chunk` annealed sweeps and the
-// re-unitarisation that follows them), at most two chunks in flight per job,
+// re-unitarisation that follows them), at most two chunks in flight per job.
+// Chunk graphs are kept per shape (extents, precision, storage, staple kind,
+// chunk length): a finished job returns its instantiated graph to the pool of
+// its shape, and the next job of that shape updates it in place with its own
+// field pointers and parameters (cudaGraphExecUpdate of a fresh capture, which
+// costs less than instantiating the graph anew),
 // so the work of all running jobs overlaps on the device and a job that
 // arrives while others run is admitted as soon as a slot and memory free up.
 // Kernels are deterministic and jobs share no device memory, so a job's
@@ -26,6 +31,15 @@ namespace vs {
 
 enum JobState { WAITING, RUNNING, DONE };
 
+// What fixes the node structure of a job's chunk graph.
+struct GraphKey {
+    int32_t dims[4];
+    int32_t precision, storage, rect, chunk, reunit_every;
+    bool operator<(const GraphKey &o) const {
+        return std::memcmp(this, &o, sizeof *this) < 0;
+    }
+};
+
 struct Job {
     int64_t ticket = 0;
     vs_job spec{};
@@ -39,6 +53,7 @@ struct Job {
     int sweeps_enqueued = 0;
     int chunk = 10;
     cudaGraphExec_t graph = nullptr;
+    GraphKey key{};
     std::deque<cudaEvent_t> inflight;
     vs_result result{};
 };
@@ -55,6 +70,8 @@ struct Serve {
     int n_levels = 1;
     std::vector<bool> slot_busy;
     std::vector<cudaEvent_t> event_pool;
+    std::map<GraphKey, std::vector<cudaGraphExec_t>> graph_pool;   // idle chunk graphs per shape
+    int64_t graphs_instantiated = 0, graphs_reused = 0;
     int64_t next_ticket = 1;
     uint64_t bytes_in_use = 0, peak_bytes = 0;
     int64_t n_submitted = 0, n_completed = 0, n_cancelled = 0;
@@ -66,6 +83,7 @@ struct Serve {
     void step_running(std::unique_lock<std::mutex> &lk, bool &progressed);
     void finish(Job &j, vs_status st);
     cudaEvent_t get_event();
+    cudaGraphExec_t take_graph(const GraphKey &k);
 };
 
 static double now_ms(vs_ctx *c) { return vs_now_ms(c); }
@@ -161,7 +179,8 @@ void Serve::finish(Job &j, vs_status st) {
         j.f = nullptr;
     }
     if (j.graph) {
-        cudaGraphExecDestroy(j.graph);
+        // idle now (the job's chunks have completed): the next job of this shape updates it
+        graph_pool[j.key].push_back(j.graph);
         j.graph = nullptr;
     }
     for (auto e : j.inflight) event_pool.push_back(e);
@@ -173,8 +192,17 @@ void Serve::finish(Job &j, vs_status st) {
     cv_work.notify_all();
 }
 
+// An idle chunk graph of the job's shape, or nullptr (lock held).
+cudaGraphExec_t Serve::take_graph(const GraphKey &k) {
+    auto it = graph_pool.find(k);
+    if (it == graph_pool.end() || it->second.empty()) return nullptr;
+    cudaGraphExec_t g = it->second.back();
+    it->second.pop_back();
+    return g;
+}
+
 // Enqueue the next chunk of a running job (lock released by caller).
-static vs_status enqueue_chunk(Job &j, unsigned long long *ctr) {
+static vs_status enqueue_chunk(Serve &sv, std::unique_lock<std::mutex> &lk, Job &j, unsigned long long *ctr) {
     NvtxRange range("vs served chunk");
     vs_field *f = j.f;
     const vs_job &s = j.spec;
@@ -197,9 +225,29 @@ static vs_status enqueue_chunk(Job &j, unsigned long long *ctr) {
                 return st;
             }
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&j.graph, g, 0);
+            j.key = GraphKey{{s.dims[0], s.dims[1], s.dims[2], s.dims[3]}, s.precision, s.storage,
+                             s.epsilon != 1.0, j.chunk, s.reunit_every};
+            lk.lock();
+            cudaGraphExec_t pooled = sv.take_graph(j.key);
+            lk.unlock();
+            bool reused = false;
+            if (pooled) {
+                // same node structure, this job's pointers and parameters
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(pooled, g, &info) == cudaSuccess) {
+                    j.graph = pooled;
+                    reused = true;
+                } else {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(pooled);
+                }
+            }
+            if (!reused) e = cudaGraphInstantiate(&j.graph, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            lk.lock();
+            ++(reused ? sv.graphs_reused : sv.graphs_instantiated);
+            lk.unlock();
         }
         cudaError_t e = cudaGraphLaunch(j.graph, f->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
@@ -242,7 +290,7 @@ void Serve::step_running(std::unique_lock<std::mutex> &lk, bool &progressed) {
             if (j.inflight.size() < 2) {
                 cudaEvent_t ev = get_event();
                 lk.unlock();
-                vs_status st = enqueue_chunk(j, j.f->d_sweep);
+                vs_status st = enqueue_chunk(*this, lk, j, j.f->d_sweep);
                 if (st == VS_OK && cudaEventRecord(ev, j.stream) != cudaSuccess)
                     st = fail(VS_EDEVICE, "event record failed");
                 lk.lock();
@@ -338,6 +386,8 @@ void serve_shutdown(vs_ctx *c) {
         for (auto e : j.inflight) cudaEventDestroy(e);
     }
     for (auto e : s->event_pool) cudaEventDestroy(e);
+    for (auto &kv : s->graph_pool)
+        for (auto g : kv.second) cudaGraphExecDestroy(g);
     for (auto st : s->streams) cudaStreamDestroy(st);
     delete s;
     c->serve = nullptr;
@@ -432,5 +482,7 @@ extern "C" vs_status vs_serve_stats_get(vs_ctx *c, vs_serve_stats *out) {
     out->waiting = (int64_t)s->waiting.size();
     out->bytes_in_use = s->bytes_in_use;
     out->peak_bytes_in_use = s->peak_bytes;
+    out->graphs_instantiated = s->graphs_instantiated;
+    out->graphs_reused = s->graphs_reused;
     return VS_OK;
 }

@@ -96,7 +96,8 @@ class vs_serve_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("cancelled", ctypes.c_int64), ("running", ctypes.c_int64),
                 ("waiting", ctypes.c_int64), ("bytes_in_use", ctypes.c_uint64),
-                ("peak_bytes_in_use", ctypes.c_uint64)]
+                ("peak_bytes_in_use", ctypes.c_uint64), ("graphs_instantiated", ctypes.c_int64),
+                ("graphs_reused", ctypes.c_int64)]
 
 
 P = ctypes.c_void_p

