@@ -295,6 +295,13 @@ def run_ours(args):
         except Exception as e:  # report it, keep the main line
             line["fp64_plain"] = {"error": repr(e)}
 
+    # ---- per-sweep vortex diagnostics of the workload, VP on and off -------
+    if not args.no_other:
+        try:
+            line["vortex_diagnostics"] = vortex_diagnostics(vs, ctx, stream, labels_dev, args)
+        except Exception as e:
+            line["vortex_diagnostics"] = {"error": repr(e)}
+
     # ---- the paper's other smoothing paths on the same field ---------------
     if not args.no_other:
         try:
@@ -389,6 +396,34 @@ def fp64_plain(vs, ctx, stream, labels_dev, args, value, world, dev):
             "fp32_same_scope": {"value": v32, "ms": ms["fp32"]}, "fp32_over_fp64": v32 / v64,
             "scope": "vs_smooth sweeps alone in both precisions (class updates, and FP32 "
                      "re-unitarisation every 10 sweeps), same field and sweep count"}
+
+
+def vortex_diagnostics(vs, ctx, stream, labels_dev, args):
+    """The workload's sweeps with and without vortex preservation (Sec. VI),
+    per-sweep statistics from the kernels: candidates whose Z(3) label differs
+    from the original (without VP: the label differences after the sweep, the
+    n_diff of the paper's tables), candidates inside the FP32 rounding band of a
+    sector edge, the smallest candidate margin, and the action."""
+    out = {}
+    marks = [k for k in (1, 2, 5, 10, 20, 50, 100, 200, 300) if k <= args.sweeps]
+    for vp in (True, False):
+        f = vs.vs_field_create(ctx, DIMS, vs.VS_FP32, vs.VS_LINK18, stream)
+        vs.vs_load_field(f, labels=labels_dev)
+        vs.vs_centrifuge(f, OMEGA, CENTRIFUGE_SEED)
+        st = vs.vs_smooth(f, args.sweeps, RHO, EPS, U0, reunit_every=REUNIT, vortex_preserve=vp,
+                          action_every=1, stats=True)
+        chk = vs.vs_vortex_check(f)
+        vs.vs_field_destroy(f)
+        out["vp_on" if vp else "vp_off"] = {
+            "n_label_diff_at_sweep": {str(k): st[k - 1]["n_label_diff"] for k in marks},
+            "action_at_sweep": {str(k): st[k - 1]["action"] for k in marks},
+            "min_margin_at_sweep": {str(k): st[k - 1]["min_margin"] for k in marks},
+            "n_undecidable_total": int(sum(s["n_undecidable"] for s in st)),
+            "n_fp64_exp_total": int(sum(s["n_fp64_exp"] for s in st)),
+            "after_last_sweep": {"n_label_diff": chk["n_label_diff"], "n_charge_diff": chk["n_charge_diff"]}}
+    out["what"] = ("%d sweeps of the workload (FP32 18-real) with per-sweep statistics; with VP the "
+                   "candidate label differences are the rejections" % args.sweeps)
+    return out
 
 
 def other_paths(vs, ctx, stream, labels_dev, args, world, dev):
