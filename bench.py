@@ -623,10 +623,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_rate(dims):
+    """The FP64 oracle on the host cores: one annealed over-improved VP sweep
+    of `dims` from iid uniform Z(3) labels after the centrifuge (its cost per
+    link does not depend on the label values)."""
+    import oracle as O
+    import synth
+    V = int(np.prod(dims))
+    lab = synth.iid_labels(dims, 5, p0=1 / 3, p_plus=1 / 3)
+    Uc = O.centrifuge(dims, lab, OMEGA, CENTRIFUGE_SEED)
+    t0 = time.perf_counter()
+    O.smooth(dims, Uc, lab, 1, RHO, eps=EPS, vp=True, nthreads=O.max_threads())
+    dt = time.perf_counter() - t0
+    return {"value": 4 * V / dt, "unit": "link-updates/s", "cores": O.max_threads(), "seconds": dt,
+            "sample": "1 annealed over-improved VP sweep from iid uniform labels after the centrifuge"}
+
+
 def run_scaling(args):
     """Lattice-size sweep (16^3x32 .. 48^3x96): link-updates/s and the roofline
-    fraction of the class-update kernel per size, FP32 18- and 12-real; one
-    JSON line per size."""
+    fraction of the class-update kernel per size, FP32 18- and 12-real, beside
+    the FP64 oracle on the host cores (one sweep per size, --no-cpu-baseline
+    skips it); one JSON line per size and storage."""
     import torch
     from paper_2203_09764_gb300 import vs
     stream = torch.cuda.Stream()
@@ -634,6 +651,7 @@ def run_scaling(args):
     ctx = vs.vs_create(0)
     peaks, src = _measured_peaks()
     for dims in [(16, 16, 16, 32), (24, 24, 24, 48), (32, 32, 32, 64), (40, 40, 40, 80), (48, 48, 48, 96)]:
+        orc = None if args.no_cpu_baseline else _oracle_rate(dims)
         for storage, nc in ((vs.VS_LINK18, 18), (vs.VS_LINK12, 12)):
             V = int(np.prod(dims))
             f = vs.vs_field_create(ctx, dims, vs.VS_FP32, storage, stream)
@@ -654,11 +672,13 @@ def run_scaling(args):
             per = cms / nl
             bpu = BYTES_PER_UPDATE[(1, nc)]
             ach = V / 4 * bpu / (per / 1e3) / 1e9
+            rate = 4 * V * args.sweeps / (ms / 1e3)
             print(json.dumps({"lattice": list(dims), "storage": "%d-real" % nc, "sweeps": args.sweeps,
-                              "link_updates_per_s": 4 * V * args.sweeps / (ms / 1e3),
+                              "link_updates_per_s": rate,
                               "class_launch_ms": per, "achieved_gbs": ach,
                               "hbm_frac": ach / peaks["hbm_gbs"], "peak_source": src,
-                              "field_mb": 4 * nc * 4 * V / 1e6}), flush=True)
+                              "field_mb": 4 * nc * 4 * V / 1e6, "oracle_host": orc,
+                              "gpu_over_oracle": rate / orc["value"] if orc else None}), flush=True)
     vs.vs_destroy(ctx)
 
 
