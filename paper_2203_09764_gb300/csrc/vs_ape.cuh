@@ -197,7 +197,7 @@ __device__ __forceinline__ void flow_finish(const FlowParams &a, int i, const M3
 __device__ __forceinline__ void flow_count(const FlowParams &a, bool used64) {
     if (a.counters) {
         const unsigned fb = __ballot_sync(0xffffffffu, used64);
-        if ((threadIdx.x & 31) == 0 && fb) atomicAdd(&a.counters[1], (unsigned long long)__popc(fb));
+        if ((threadIdx.x & 31) == 0 && fb) atomicAdd(&a.counters[kCntSecond], (unsigned long long)__popc(fb));
     }
 }
 

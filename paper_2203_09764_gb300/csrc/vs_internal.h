@@ -55,7 +55,7 @@ struct AusParams {
     float alpha_f, c0_f, c1_f;
     int n_hits;
     int vp;
-    unsigned long long *counters;  // [0] rejects (may be null)
+    unsigned long long *counters;  // kSweepSlots counters of the sweep (kCnt*), or null
 };
 
 // One colour class (or, colour < 0, every link of direction mu) of APE
@@ -72,7 +72,7 @@ struct ApeParams {
     double alpha, c0, c1;
     float alpha_f, c0_f, c1_f;
     int vp;
-    unsigned long long *counters;  // [0] rejects, [1] singular blocked matrices (may be null)
+    unsigned long long *counters;  // kSweepSlots counters of the sweep (kCntSecond: singular), or null
 };
 
 // One stage of the third-order Runge-Kutta Wilson flow for every link of
@@ -86,7 +86,7 @@ struct FlowParams {
     int n_threads;
     double h, a, b, c, c0, c1;
     float h_f, a_f, b_f, c_f, c0_f, c1_f;
-    unsigned long long *counters;  // [1] FP64 exponentials (may be null)
+    unsigned long long *counters;  // kCntSecond: FP64 exponentials of the step (may be null)
 };
 
 cudaError_t launch_ape_f18(bool rect, int mu, const ApeParams &p, cudaStream_t st);

@@ -881,3 +881,39 @@ def test_per_sweep_label_diffs_and_margins_fp64(ctx, vp):
         assert abs(st[k]["min_margin"] - float(np.nanmin(cm))) < 1e-10
         n_diff_seen += want_diff
     assert n_diff_seen > 0
+
+
+@pytest.mark.parametrize("method", ["aus", "ucp"])
+@pytest.mark.parametrize("vp", [True, False])
+def test_aus_and_ucp_per_sweep_label_diffs_fp64(ctx, method, vp):
+    """The per-sweep diagnostics of vs_smooth_aus / vs_smooth_ape in the
+    paper's AS setting (alpha = 0.7, a random gauge, Sec. V.D and Table
+    t:recipes), FP64 against the oracle one sweep at a time: the candidates'
+    label differences (in the original gauge, Sec. VI) equal the oracle's
+    rejections with vortex preservation, and without it the label differences
+    after the sweep; no candidate lies within the FP64 band of an edge."""
+    dims = (8, 8, 8, 8)
+    lab = cooled_labels(dims, 2)
+    G = synth.random_gauge(dims, 43)
+    U = O.gauge_transform(dims, O.centrifuge(dims, lab, 0.02, 1234), G)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP64, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=lab)
+    vs.vs_centrifuge(f, 0.02, 1234)
+    vs.vs_gauge_transform(f, G)
+    if method == "aus":
+        st = vs.vs_smooth_aus(f, 3, 0.7, -0.25, vortex_preserve=vp, stats=True)
+    else:
+        st = vs.vs_smooth_ape(f, 3, 0.7, -0.25, vortex_preserve=vp, stats=True)
+    vs.vs_field_destroy(f)
+    seen = 0
+    for k in range(3):
+        if method == "aus":
+            U, rej = O.aus(dims, U, lab, 1, 0.7, eps=-0.25, vp=vp, gauge=G)
+        else:
+            U, rej = O.ape_ucp(dims, U, lab, 1, 0.7, eps=-0.25, vp=vp, gauge=G)
+        want = int(rej[0]) if vp else O.vortex_check(dims, U, lab, gauge=G)["n_label_diff"]
+        assert st[k]["n_label_diff"] == want, (k, st[k], want)
+        assert st[k]["n_reject"] == (int(rej[0]) if vp else 0)
+        assert st[k]["n_undecidable"] == 0 and 0 < st[k]["min_margin"] < np.pi / 3 + 1e-12
+        seen += want
+    assert seen > 0
