@@ -90,8 +90,9 @@ void vs_destroy(vs_ctx *ctx);
 /* Allocate a field (links + resident reference labels) on the context's
  * device.  stream: a cudaStream_t to run on, or NULL for a library-owned
  * stream.  EINVAL: an extent not a positive multiple of 4, more than 2^30
- * sites, or an unknown precision/storage; EUNSUPPORTED: FP64 with 12-real
- * storage. */
+ * plane positions (sites, plus the layout's unused positions when Lx/4 is 5,
+ * 6 or 7; see vs_field_describe), or an unknown precision/storage;
+ * EUNSUPPORTED: FP64 with 12-real storage. */
 vs_status vs_field_create(vs_ctx *ctx, const int32_t dims[4], int32_t precision,
                           int32_t storage, void *stream, vs_field **out);
 /* Device memory of a field: the links (4 V x 18 or 12 reals), two label planes
@@ -367,7 +368,7 @@ typedef struct {
     int32_t dims[4];
     int32_t precision, storage;
     int64_t n_sites;
-    int64_t plane_stride;          /* P: sites per vector plane */
+    int64_t plane_stride;          /* P: positions per vector plane, n_sites or more (see below) */
     int32_t n_components;          /* NC: 18 or 12 stored reals per link */
     int32_t device;                /* CUDA device ordinal that holds the field */
     void *links;                   /* device: direction mu at element mu*NC*P, split into
@@ -385,10 +386,14 @@ typedef struct {
 
 /* Device layout of a field.  Within a component plane the sites follow the
  * lexicographic rows (y, z, t), and inside each x-row the sites are grouped
- * by x mod 4: position (x mod 4) * (Lx/4) + x/4 (see vs_layout_index). */
+ * by x mod 4: position row * 4Qp + (x mod 4) * Qp + x/4 (see vs_layout_index),
+ * where Qp = Lx/4, except Qp = 8 when Lx/4 is 5, 6 or 7: a group of one
+ * colour class's sites then fills one 128-byte line of a float4 plane instead
+ * of straddling two, and the positions Lx/4 .. 7 of each group hold no link
+ * (plane_stride = 4 Qp Ly Lz Lt). */
 vs_status vs_field_describe(const vs_field *f, vs_field_desc *out);
 
-/* Position of site (x,y,z,t) inside a component plane. */
+/* Position of site (x,y,z,t) inside a component plane (layout above). */
 int64_t vs_layout_index(const int32_t dims[4], const int32_t x[4]);
 
 /* Number of kernels the library has launched directly in this process (CUDA

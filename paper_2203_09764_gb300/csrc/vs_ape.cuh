@@ -201,8 +201,8 @@ __device__ __forceinline__ void flow_count(const FlowParams &a, bool used64) {
     }
 }
 
-// One Runge-Kutta stage for every link of direction MU (thread t = plane
-// position t), staples from plain loads (FP64, and FP32 without the ring).
+// One Runge-Kutta stage for every link of direction MU (thread t = site t in
+// plane order), staples from plain loads (FP64, and FP32 without the ring).
 template <class T, int NC, bool RECT, int MU>
 __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSWEEP_MINB : 1)
     k_flow_stage(FlowParams a) {
@@ -211,12 +211,13 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     if (t < a.n_threads) {
         const Geo &g = a.g;
         const Pt x = site_of_index(g, t);
+        const int i = sidx(g, x);
         const T *Us = static_cast<const T *>(a.Usrc);
         const bool f32 = sizeof(T) == 4;
         const T c0 = f32 ? T(a.c0_f) : T(a.c0), c1 = f32 ? T(a.c1_f) : T(a.c1);
         const M3<T> sig = staple_sum<T, NC, RECT, MU>(g, Us, x, c0, c1);
-        const M3<T> u = load_link<T, NC>(Us, g.P, MU, t);
-        flow_finish<T, NC, MU>(a, t, sig, u, used64);
+        const M3<T> u = load_link<T, NC>(Us, g.P, MU, i);
+        flow_finish<T, NC, MU>(a, i, sig, u, used64);
     }
     flow_count(a, used64);
 }
@@ -234,22 +235,23 @@ __global__ void __launch_bounds__(VS_RING_THREADS, RECT ? VS_RING_MINB : 4) k_fl
     if (t < a.n_threads) {
         const Geo &g = a.g;
         const Pt x = site_of_index(g, t);
+        const int i = sidx(g, x);
         const float *Us = static_cast<const float *>(a.Usrc);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> sig, u;
         // the exponent H_S of this link, read before the staple stream so that
         // its latency hides behind it (stage 1 of a step does not read it)
         float s_old[9];
-        const float *Sp = static_cast<const float *>(a.S) + (long long)MU * 9 * g.P + t;
+        const float *Sp = static_cast<const float *>(a.S) + (long long)MU * 9 * g.P + i;
 #pragma unroll
         for (int k = 0; k < 9; ++k) s_old[k] = a.b_f != 0.0f ? __ldg(Sp + (long long)k * g.P) : 0.0f;
         if constexpr (RECT) {
             sig = staple_sum_fused<NC, MU>(g, Us, x, a.c0_f, a.c1_f, R, u);
         } else {
             sig = staple_sum_plain_ring<NC, MU>(g, Us, x, a.c0_f, R);
-            u = load_link<float, NC>(Us, g.P, MU, t);
+            u = load_link<float, NC>(Us, g.P, MU, i);
         }
-        flow_finish<float, NC, MU>(a, t, sig, u, used64, s_old);
+        flow_finish<float, NC, MU>(a, i, sig, u, used64, s_old);
     }
     flow_count(a, used64);
 }

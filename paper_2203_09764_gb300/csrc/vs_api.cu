@@ -108,22 +108,24 @@ static size_t field_bytes(const vs_field *f) {
     return (size_t)4 * f->nc * (size_t)f->g.P * (f->prec == VS_FP64 ? 8 : 4);
 }
 
-// Extents: positive multiples of 4 (the colour classes), at most 2^30 sites so
-// that plane positions and per-site loop indices fit in 32-bit ints.
-static bool valid_dims(const int32_t d[4]) {
-    long long v = 1;
+// Extents: positive multiples of 4 (the colour classes), at most 2^30 plane
+// positions (the sites and the layout's unused positions, make_geo) so that
+// positions and per-site loop indices fit in 32-bit ints.
+bool vs::valid_dims(const int32_t d[4]) {
+    long long p = 1;
     for (int k = 0; k < 4; ++k) {
-        if (d[k] < 4 || d[k] % 4) return false;
-        v *= d[k];
+        if (d[k] < 4 || d[k] % 4 || d[k] > (1 << 30)) return false;
+        p *= k == 0 ? 4 * ((d[0] / 4 == 5 || d[0] / 4 == 6 || d[0] / 4 == 7) ? 8 : d[0] / 4) : d[k];
+        if (p > (1ll << 30)) return false;
     }
-    return v <= (1ll << 30);
+    return true;
 }
 
 uint64_t vs::field_footprint(const int32_t dims[4], int32_t precision, int32_t storage) {
-    long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    const long long P = make_geo(dims).P;   // plane stride, with the layout's unused positions
     int nc = storage == VS_LINK12 ? 12 : 18;
-    uint64_t links = (uint64_t)4 * nc * V * (precision == VS_FP64 ? 8 : 4);
-    return links + 8ull * V + 1216 * 8 + 4096;
+    uint64_t links = (uint64_t)4 * nc * P * (precision == VS_FP64 ? 8 : 4);
+    return links + 8ull * P + 1216 * 8 + 4096;
 }
 
 extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t precision, int32_t storage,
@@ -132,7 +134,7 @@ extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t p
     *out = nullptr;
     if (!valid_dims(dims))
         return fail(VS_EINVAL,
-                    "vs_field_create: extents must be positive multiples of 4 with at most 2^30 sites "
+                    "vs_field_create: extents must be positive multiples of 4 with at most 2^30 layout positions "
                     "(got %d %d %d %d)", dims[0], dims[1], dims[2], dims[3]);
     if (precision != VS_FP64 && precision != VS_FP32) return fail(VS_EINVAL, "vs_field_create: bad precision");
     if (storage != VS_LINK18 && storage != VS_LINK12) return fail(VS_EINVAL, "vs_field_create: bad storage");
@@ -144,10 +146,7 @@ extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t p
     f->ctx = c;
     f->prec = precision;
     f->nc = storage == VS_LINK12 ? 12 : 18;
-    for (int k = 0; k < 4; ++k) f->g.L[k] = dims[k];
-    f->g.Q = dims[0] / 4;
-    f->g.V = dims[0] * dims[1] * dims[2] * dims[3];
-    f->g.P = f->g.V;
+    f->g = make_geo(dims);
     if (stream) {
         f->stream = (cudaStream_t)stream;
     } else {
@@ -217,9 +216,7 @@ extern "C" vs_status vs_field_describe(const vs_field *f, vs_field_desc *d) {
 }
 
 extern "C" int64_t vs_layout_index(const int32_t dims[4], const int32_t x[4]) {
-    Geo g;
-    for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
-    g.Q = dims[0] / 4;
+    const Geo g = make_geo(dims);
     return sidx(g, x[0], x[1], x[2], x[3]);
 }
 
@@ -449,7 +446,7 @@ extern "C" vs_status vs_gauge_transform(vs_field *f, const double *G, int32_t wh
     CK(cudaSetDevice(f->ctx->opt.device));
     const size_t V = f->g.V;
     if (!f->G) {
-        f->G = dev_alloc(f->ctx, V * 18 * (f->prec == VS_FP64 ? 8 : 4));
+        f->G = dev_alloc(f->ctx, (size_t)f->g.P * 18 * (f->prec == VS_FP64 ? 8 : 4));
         if (!f->G) return fail(VS_ENOMEM, "vs_gauge_transform: allocation failed");
     }
     const double *src = G;

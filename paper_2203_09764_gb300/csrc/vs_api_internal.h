@@ -77,6 +77,7 @@ vs_status cuda_fail(cudaError_t e, const char *what);
 void *dev_alloc(vs_ctx *c, size_t bytes);
 void dev_free(vs_ctx *c, void *p);
 uint64_t field_footprint(const int32_t dims[4], int32_t precision, int32_t storage);
+bool valid_dims(const int32_t dims[4]);
 
 // Enqueue n_sweeps on the field's stream.  want_stats: per-sweep counters and
 // actions into the field's stats buffers.  fixed_counters (optional): every

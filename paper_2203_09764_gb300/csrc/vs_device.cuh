@@ -6,10 +6,12 @@
 //   conj(row0 x row1) on load), split into planes of float4 / float2 /
 //   double2 vectors (see load_link); i = site position in a plane.
 //   Site position: rows (y, z, t) in lexicographic order, and inside each
-//   x-row the sites grouped by x mod 4: i = row*Lx + (x & 3)*(Lx/4) + (x >> 2).
-//   For a colour class of the annealed schedule the updated sites of one
-//   row form contiguous runs of Lx/4, so a warp's loads of any plane are
-//   whole 32-byte sectors.
+//   x-row the sites grouped by x mod 4: i = row*4Qp + (x & 3)*Qp + (x >> 2),
+//   Qp = Lx/4, or 8 when Lx/4 is 5, 6 or 7 (the group then ends in unused
+//   positions).  For a colour class of the annealed schedule the updated
+//   sites of one row form contiguous runs of Lx/4, so a warp's loads of any
+//   plane are whole 32-byte sectors; with the padding a run of 5-7 sites
+//   (80-112 bytes of a float4 plane) never straddles a 128-byte line.
 //   labels[mu][i]    int8 reference Z(3) label of link (mu, i).
 #pragma once
 
@@ -20,10 +22,24 @@ namespace vs {
 
 struct Geo {
     int L[4];       // Lx, Ly, Lz, Lt
-    int Q;          // Lx / 4
+    int Q;          // Lx / 4: sites of one x mod 4 group of an x-row
+    int Qp;         // positions of that group in the layout (Q, or 8 for Q = 5, 6, 7)
+    int Lxp;        // positions of an x-row: 4 Qp
     int V;          // sites
-    long long P;    // plane stride in elements
+    long long P;    // plane stride in sites (positions): Lxp Ly Lz Lt >= V
 };
+
+// The geometry of extents dims (each a positive multiple of 4).
+__host__ __device__ inline Geo make_geo(const int dims[4]) {
+    Geo g;
+    for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
+    g.Q = dims[0] / 4;
+    g.Qp = (g.Q == 5 || g.Q == 6 || g.Q == 7) ? 8 : g.Q;
+    g.Lxp = 4 * g.Qp;
+    g.V = (int)((long long)dims[0] * dims[1] * dims[2] * dims[3]);
+    g.P = (long long)g.Lxp * dims[1] * dims[2] * dims[3];
+    return g;
+}
 
 __host__ __device__ __forceinline__ int wrapc(int v, int L) {
     v = v < 0 ? v + L : v;
@@ -42,7 +58,7 @@ __device__ __forceinline__ Pt mv(const Geo &g, Pt p, int d, int k) {
 }
 
 __host__ __device__ __forceinline__ int sidx(const Geo &g, int x0, int x1, int x2, int x3) {
-    return ((x3 * g.L[2] + x2) * g.L[1] + x1) * g.L[0] + (x0 & 3) * g.Q + (x0 >> 2);
+    return ((x3 * g.L[2] + x2) * g.L[1] + x1) * g.Lxp + (x0 & 3) * g.Qp + (x0 >> 2);
 }
 __device__ __forceinline__ int sidx(const Geo &g, const Pt &p) { return sidx(g, p.x0, p.x1, p.x2, p.x3); }
 
@@ -50,7 +66,8 @@ __device__ __forceinline__ int lexidx(const Geo &g, const Pt &p) {
     return p.x0 + g.L[0] * (p.x1 + g.L[1] * (p.x2 + g.L[2] * p.x3));
 }
 
-// site at plane position i
+// Site number i (0 <= i < V) in plane order, i.e. the i-th site of the
+// layout skipping unused positions (its position is sidx of the result).
 __device__ __forceinline__ Pt site_of_index(const Geo &g, int i) {
     Pt p;
     int w = i % g.L[0];

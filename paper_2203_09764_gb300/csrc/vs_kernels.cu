@@ -102,7 +102,7 @@ __global__ void k_count_nonfinite(Geo g, const T *__restrict__ U, unsigned long 
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool bad = false;
     if (l < 4ll * g.V) {
-        const M3<T> m = load_link<T, NC>(U, g.P, (int)(l / g.V), (int)(l % g.V));
+        const M3<T> m = load_link<T, NC>(U, g.P, (int)(l / g.V), sidx(g, site_of_index(g, (int)(l % g.V))));
 #pragma unroll
         for (int k = 0; k < 9; ++k) bad |= !isfinite(m.re[k]) || !isfinite(m.im[k]);
     }
@@ -222,8 +222,9 @@ __device__ __forceinline__ double block_sum(double v) {
 template <class T, int NC>
 __global__ void __launch_bounds__(kThreads) k_action(Geo g, const T *__restrict__ U, double *partials) {
     double acc = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.V; i += gridDim.x * blockDim.x) {
-        Pt x = site_of_index(g, i);
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < g.V; d += gridDim.x * blockDim.x) {
+        const Pt x = site_of_index(g, d);
+        const int i = sidx(g, x);
 #pragma unroll
         for (int mu = 0; mu < 3; ++mu) {
             M3<T> Umu = load_link<T, NC>(U, g.P, mu, i);
@@ -318,8 +319,9 @@ __global__ void __launch_bounds__(kThreads) k_observables(Geo g, const T *__rest
     double aS = 0, aSR = 0, aQ = 0;
     const int pairs[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
     const double sgn[3] = {1.0, -1.0, 1.0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.V; i += gridDim.x * blockDim.x) {
-        const Pt x = site_of_index(g, i);
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < g.V; d += gridDim.x * blockDim.x) {
+        const Pt x = site_of_index(g, d);
+        const int i = sidx(g, x);
         double s = 0, sr = 0, q = 0;
         for (int pp = 0; pp < 3; ++pp) {
             T r1, r2;
@@ -427,10 +429,12 @@ __global__ void k_vortex_links(Geo g, const T *__restrict__ U, const int8_t *__r
     bool diff = false, near = false;
     double margin = 1e300;
     if (l < 4ll * g.V) {
-        int mu = (int)(l / g.V), i = (int)(l % g.V);
+        const int mu = (int)(l / g.V);
+        const Pt x = site_of_index(g, (int)(l % g.V));
+        const int i = sidx(g, x);
         M3<T> m = load_link<T, NC>(U, g.P, mu, i);
         T a, b;
-        vp_trace<T>(G, g.P, i, G ? sidx(g, mv(g, site_of_index(g, i), mu, 1)) : i, m, a, b);
+        vp_trace<T>(G, g.P, i, G ? sidx(g, mv(g, x, mu, 1)) : i, m, a, b);
         int lab = z3_label<T>(a, b);
         cur[(long long)mu * g.P + i] = (int8_t)lab;
         diff = lab != ref[(long long)mu * g.P + i];
@@ -466,10 +470,11 @@ __device__ __forceinline__ int charge(const Geo &g, const int8_t *lab, const Pt 
 
 __global__ void k_vortex_charges(Geo g, const int8_t *__restrict__ ref, const int8_t *__restrict__ cur,
                                  unsigned long long *counts) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int dn = blockIdx.x * blockDim.x + threadIdx.x;
     int nd = 0;
-    if (i < g.V) {
-        Pt x = site_of_index(g, i);
+    if (dn < g.V) {
+        const Pt x = site_of_index(g, dn);
+        const int i = sidx(g, x);
         for (int mu = 0; mu < 4; ++mu)
             for (int nu = mu + 1; nu < 4; ++nu)
                 nd += charge(g, cur, x, i, mu, nu) != charge(g, ref, x, i, mu, nu);
@@ -495,7 +500,9 @@ template <class T, int NC>
 __global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref, const T *__restrict__ G) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= 4ll * g.V) return;
-    int mu = (int)(l / g.V), i = (int)(l % g.V);
+    const int mu = (int)(l / g.V);
+    const Pt x = site_of_index(g, (int)(l % g.V));
+    const int i = sidx(g, x);
     M3<T> m = load_link<T, NC>(U, g.P, mu, i);
     T n0 = T(0);
 #pragma unroll
@@ -530,7 +537,7 @@ __global__ void k_reunit(Geo g, T *U, const int8_t *__restrict__ ref, const T *_
     }
     if (ref) {
         T a, b;
-        vp_trace<T>(G, g.P, i, G ? sidx(g, mv(g, site_of_index(g, i), mu, 1)) : i, m, a, b);
+        vp_trace<T>(G, g.P, i, G ? sidx(g, mv(g, x, mu, 1)) : i, m, a, b);
         if (z3_label<T>(a, b) != (int)ref[(long long)mu * g.P + i]) return;
     }
     store_link<T, NC>(U, g.P, mu, i, m);
@@ -641,8 +648,10 @@ template <class T, int NC>
 __global__ void k_gauge_links(Geo g, const T *__restrict__ Gs, T *U) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= 4ll * g.V) return;
-    int mu = (int)(l / g.V), i = (int)(l % g.V);
-    const int iy = sidx(g, mv(g, site_of_index(g, i), mu, 1));
+    const int mu = (int)(l / g.V);
+    const Pt x = site_of_index(g, (int)(l % g.V));
+    const int i = sidx(g, x);
+    const int iy = sidx(g, mv(g, x, mu, 1));
     M3<T> u = load_link<T, NC>(U, g.P, mu, i);
     u = m3_mul(load_link<T, 18>(Gs, g.P, 0, i), u);
     u = m3_mul_nd(u, load_link<T, 18>(Gs, g.P, 0, iy));
@@ -654,7 +663,8 @@ template <class T, int NC>
 __global__ void k_project(Geo g, T *U, int8_t *ref) {
     long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= 4ll * g.V) return;
-    int mu = (int)(l / g.V), i = (int)(l % g.V);
+    const int mu = (int)(l / g.V);
+    const int i = sidx(g, site_of_index(g, (int)(l % g.V)));
     M3<T> m = load_link<T, NC>(U, g.P, mu, i);
     int n = z3_label<T>(m.re[0] + m.re[4] + m.re[8], m.im[0] + m.im[4] + m.im[8]);
     double sn, cs;

@@ -130,17 +130,19 @@ extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *re
         return fail(VS_EINVAL, "vs_vortex_check_noalloc: bad storage");
     if (precision == VS_FP64 && storage == VS_LINK12)
         return fail(VS_EUNSUPPORTED, "vs_vortex_check_noalloc: 12-real storage is FP32 only");
-    long long V = 1;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 4; ++k)
         if (dims[k] < 4 || dims[k] % 4)
             return fail(VS_EINVAL, "vs_vortex_check_noalloc: extents must be positive multiples of 4");
-        V *= dims[k];
-    }
-    if (4 * V > (long long)VS_NOALLOC_MAX_LINKS)
+    // the scratch label plane is indexed like the field's: 4 x plane stride
+    // positions (the sites, plus the layout's unused positions when Lx/4 is
+    // 5, 6 or 7)
+    const Geo g = make_geo(dims);
+    if (4 * g.P > (long long)VS_NOALLOC_MAX_LINKS)
         return fail(VS_EINVAL,
-                    "vs_vortex_check_noalloc: %lld links exceed the fixed scratch of %lld links "
-                    "(at most %lld sites); use vs_vortex_check for larger lattices",
-                    4 * V, (long long)VS_NOALLOC_MAX_LINKS, (long long)VS_NOALLOC_MAX_LINKS / 4);
+                    "vs_vortex_check_noalloc: %lld link positions exceed the fixed scratch of %lld "
+                    "(at most %lld sites, e.g. 32^3 x 64); use vs_vortex_check for larger lattices",
+                    4 * g.P, (long long)VS_NOALLOC_MAX_LINKS, (long long)VS_NOALLOC_MAX_LINKS / 4);
+    const long long V = g.V;
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "vs_vortex_check_noalloc: cudaGetDevice");
@@ -157,11 +159,6 @@ extern "C" vs_status vs_vortex_check_noalloc(const void *links, const int8_t *re
                         "have not finished; the shared scratch stays in use until they do", dev);
         d.stale = 0;
     }
-    Geo g;
-    for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
-    g.Q = dims[0] / 4;
-    g.V = (int)V;
-    g.P = V;
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned long long seq = ++d.seq;
     // counters start at zero, the minimum margin at a huge value; the label

@@ -398,12 +398,8 @@ void serve_shutdown(vs_ctx *c) {
 extern "C" vs_status vs_submit(vs_ctx *c, const vs_job *job, int64_t *ticket) {
     if (!c || !job || !ticket) return fail(VS_EINVAL, "vs_submit: NULL argument");
     int32_t d[4] = {job->dims[0], job->dims[1], job->dims[2], job->dims[3]};
-    long long sites = 1;
-    for (int k = 0; k < 4; ++k) {
-        if (d[k] < 4 || d[k] % 4) return fail(VS_EINVAL, "vs_submit: extents must be positive multiples of 4");
-        sites *= d[k];
-    }
-    if (sites > (1ll << 30)) return fail(VS_EINVAL, "vs_submit: more than 2^30 sites");
+    if (!valid_dims(d))
+        return fail(VS_EINVAL, "vs_submit: extents must be positive multiples of 4 with at most 2^30 layout positions");
     if (job->precision != VS_FP32 && job->precision != VS_FP64) return fail(VS_EINVAL, "vs_submit: bad precision");
     if (job->storage != VS_LINK18 && job->storage != VS_LINK12) return fail(VS_EINVAL, "vs_submit: bad storage");
     if (job->precision == VS_FP64 && job->storage == VS_LINK12) return fail(VS_EUNSUPPORTED, "vs_submit: FP64 12-real");

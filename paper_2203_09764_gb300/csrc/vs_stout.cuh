@@ -39,19 +39,19 @@ template <> struct Tol<float> { static __device__ __forceinline__ float eps() { 
 template <> struct Tol<double> { static __device__ __forceinline__ double eps() { return 1e-17; } };
 
 // The plane position is a sum of one term per coordinate,
-//   i(x) = Xpos(x0) + Lx x1 + Lx Ly x2 + Lx Ly Lz x3,  Xpos(x0) = (x0 & 3) Lx/4 + x0/4,
+//   i(x) = Xpos(x0) + Lxp x1 + Lxp Ly x2 + Lxp Ly Lz x3,  Xpos(x0) = (x0 & 3) Qp + x0/4,
 // so the position of x + a e_nu + b e_mu is i(x) + D_nu(a) + D_mu(b) with
 // D_d(a) = i(x + a e_d) - i(x) for the periodic shift along d alone.
 __device__ __forceinline__ int shift_delta(const Geo &g, const Pt &x, int d, int a) {
     if (d == 0) {
         const int xn = wrapc(x.x0 + a, g.L[0]);
-        return ((xn & 3) - (x.x0 & 3)) * g.Q + ((xn >> 2) - (x.x0 >> 2));
+        return ((xn & 3) - (x.x0 & 3)) * g.Qp + ((xn >> 2) - (x.x0 >> 2));
     }
     // explicit selects: indexing the kernel-parameter array with a runtime d
     // would force a copy of the parameters to local memory
     const int xd = d == 1 ? x.x1 : (d == 2 ? x.x2 : x.x3);
     const int Ld = d == 1 ? g.L[1] : (d == 2 ? g.L[2] : g.L[3]);
-    const int st = d == 1 ? g.L[0] : (d == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2]);
+    const int st = d == 1 ? g.Lxp : (d == 2 ? g.Lxp * g.L[1] : g.Lxp * g.L[1] * g.L[2]);
     return (wrapc(xd + a, Ld) - xd) * st;
 }
 

@@ -53,6 +53,25 @@ def test_layout_index_groups_x_by_residue(libvs):
     assert seen == set(range(8 * 4 * 4 * 8))
 
 
+@pytest.mark.parametrize("Lx,Qp", [(20, 8), (24, 8), (28, 8), (12, 3), (16, 4), (48, 12)])
+def test_layout_index_pads_short_groups_to_a_line(libvs, Lx, Qp):
+    """Rows whose x mod 4 groups hold 5, 6 or 7 sites get 8 positions per
+    group (a float4 plane's 128-byte line), the others none; positions stay
+    distinct and inside the plane."""
+    from paper_2203_09764_gb300 import vs
+    dims = (Lx, 4, 4, 4)
+    seen = set()
+    for t in range(4):
+        for z in range(4):
+            for y in range(4):
+                row = y + 4 * (z + 4 * t)
+                for x in range(Lx):
+                    i = vs.vs_layout_index(dims, (x, y, z, t))
+                    assert i == row * 4 * Qp + (x % 4) * Qp + x // 4
+                    seen.add(i)
+    assert len(seen) == Lx * 64 and max(seen) < 4 * Qp * 64
+
+
 def test_version_and_error_string(libvs):
     from paper_2203_09764_gb300 import vs
     assert "sm_103a" in vs.vs_version()

@@ -81,7 +81,14 @@ def test_served_job_equals_direct_field_pipeline():
 
 def test_admission_respects_budget_and_slots():
     dims = (12, 12, 12, 24)
-    one = 4 * 18 * 4 * 41472 + 8 * 41472 + 1216 * 8 + 4096 + 4 * 41472
+    # a job's device footprint: links and two label planes over the layout's
+    # plane stride, the partials, and the host-label staging
+    ctx = vs.vs_create(0)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    P = vs.vs_field_describe(f)["plane_stride"]
+    vs.vs_field_destroy(f)
+    vs.vs_destroy(ctx)
+    one = 4 * 18 * 4 * P + 8 * P + 1216 * 8 + 4096 + 4 * 41472
     budget = int(2.5 * one)
     ctx = vs.vs_create(0, hbm_budget_bytes=budget, max_slots=8)
     ts = []
