@@ -1,16 +1,16 @@
 """The 16^3 x 32 workload in full: cooled hot start (seed 2), centrifuge
 (omega = 0.02), then 200 annealed over-improved stout sweeps (eps = -0.25,
 rho = 0.06, u0 = 1) with vortex preservation -- the oracle and the GPU in FP64
-and in FP32 (18-real links, re-unitarised every 10 sweeps), sweep by sweep
+and in FP32 (18-real and 12-real links, re-unitarised every 10 sweeps), sweep by sweep
 (Sec. II.A Eqs. stout and generator, Sec. III Eq. over-improvement, Sec. V.B
 the annealed Euler flow, Sec. VI the vortex-preservation test).
 
-Asserted: the Z(3) labels and centre charges of both GPU fields equal the
+Asserted: the Z(3) labels and centre charges of every GPU field equal the
 original ones after the last sweep (bit-exact, Sec. VI), the FP64 GPU run
 tracks the oracle link by link to 1e-10 over the first 20 sweeps (before the
 flow's amplification of rounding differences, ~1.5x per sweep on these
 fields, takes over) with the same rejection counts there, and every sweep's
-action in both precisions stays within 2e-3 relative of the oracle's.
+action in every mode stays within 2e-3 relative of the oracle's.
 Recorded (printed as one JSON line): per precision, the largest link and
 relative action differences per sweep and the first sweeps at which they
 exceed 1e-5 and 1e-6.
@@ -45,8 +45,9 @@ def test_full_200_sweep_run_against_the_oracle():
     U = O.centrifuge(DIMS, lab, OMEGA, 1234)
     ctx = vs.vs_create(0)
     fields = {}
-    for name, prec in (("fp64", vs.VS_FP64), ("fp32", vs.VS_FP32)):
-        f = vs.vs_field_create(ctx, DIMS, prec, vs.VS_LINK18)
+    for name, prec, storage in (("fp64", vs.VS_FP64, vs.VS_LINK18), ("fp32", vs.VS_FP32, vs.VS_LINK18),
+                                ("fp32_12real", vs.VS_FP32, vs.VS_LINK12)):
+        f = vs.vs_field_create(ctx, DIMS, prec, storage)
         vs.vs_load_field(f, labels=lab)
         vs.vs_centrifuge(f, OMEGA, 1234)
         fields[name] = f
