@@ -371,12 +371,14 @@ typedef struct {
     int64_t plane_stride;          /* P: positions per vector plane, n_sites or more (see below) */
     int32_t n_components;          /* NC: 18 or 12 stored reals per link */
     int32_t device;                /* CUDA device ordinal that holds the field */
-    void *links;                   /* device: direction mu at element mu*NC*P, split into
-                                      vector planes: FP32 18 reals = 4 float4 planes
-                                      (complex entries 0-1, 2-3, 4-5, 6-7) + 1 float2 plane
-                                      (entry 8); FP32 12 reals = 3 float4 planes; FP64 =
-                                      9 double2 planes; a plane of w reals per site starts
-                                      at (reals before it)*P, site i at w*i inside it */
+    void *links;                   /* device: direction mu at element mu*NC*P, in blocks of
+                                      16 plane positions (16*NC reals each); inside a block
+                                      one vector chunk of the 16 links after another: FP32
+                                      18 reals = 4 float4 chunks (complex entries 0-1, 2-3,
+                                      4-5, 6-7) + 1 float2 chunk (entry 8); FP32 12 reals =
+                                      3 float4 chunks; FP64 = 9 double2 chunks (one entry
+                                      each); position i is element i mod 16 of its block's
+                                      chunks */
     int8_t *labels;                /* device: [4][plane_stride] reference labels */
     void *stream;
     void *gauge;                   /* device: the random gauge transformation G of vs_gauge_transform

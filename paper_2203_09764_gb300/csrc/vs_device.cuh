@@ -162,6 +162,16 @@ __device__ __forceinline__ f2pk pk2(float lo, float hi) {
 __device__ __forceinline__ void upk2(f2pk v, float &lo, float &hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
+__device__ __forceinline__ f2pk add2(f2pk a, f2pk b) {
+    f2pk d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2pk mul2(f2pk a, f2pk b) {
+    f2pk d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ f2pk fma2(f2pk a, f2pk b, f2pk c) {
     f2pk d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
@@ -327,6 +337,50 @@ __device__ __forceinline__ void m3_axpy(M3<T> &r, T s, const M3<T> &a) {
     for (int k = 0; k < 9; ++k) { r.re[k] = fma(s, a.re[k], r.re[k]); r.im[k] = fma(s, a.im[k], r.im[k]); }
 }
 
+// FP32 entrywise sums of matrices.  An entry's (re, im) pair is one operand
+// of a paired instruction; each half rounds like the scalar operation, so
+// the results equal the scalar ones while the issued instructions halve
+// (the class-update kernel is bound by instruction issue).
+#if VS_FFMA2
+template <>
+__device__ __forceinline__ void m3_axpy<float>(M3<float> &r, float s, const M3<float> &a) {
+    const f2pk sp = pk2(s, s);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) upk2(fma2(sp, pk2(a.re[k], a.im[k]), pk2(r.re[k], r.im[k])), r.re[k], r.im[k]);
+}
+#endif
+
+// r += a
+__device__ __forceinline__ void m3_acc_f32(M3<float> &r, const M3<float> &a) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+#if VS_FFMA2
+        upk2(add2(pk2(r.re[k], r.im[k]), pk2(a.re[k], a.im[k])), r.re[k], r.im[k]);
+#else
+        r.re[k] += a.re[k];
+        r.im[k] += a.im[k];
+#endif
+    }
+}
+
+// r = c0 a + c1 (b + d), rounded as fmaf(c0, a, c1 * (b + d))
+__device__ __forceinline__ void m3_lin3_f32(M3<float> &r, float c0, const M3<float> &a, float c1, const M3<float> &b,
+                                            const M3<float> &d) {
+#if VS_FFMA2
+    const f2pk c0p = pk2(c0, c0), c1p = pk2(c1, c1);
+#endif
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+#if VS_FFMA2
+        upk2(fma2(c0p, pk2(a.re[k], a.im[k]), mul2(c1p, add2(pk2(b.re[k], b.im[k]), pk2(d.re[k], d.im[k])))),
+             r.re[k], r.im[k]);
+#else
+        r.re[k] = fmaf(c0, a.re[k], c1 * (b.re[k] + d.re[k]));
+        r.im[k] = fmaf(c0, a.im[k], c1 * (b.im[k] + d.im[k]));
+#endif
+    }
+}
+
 template <class T>
 __device__ __forceinline__ void m3_scale(M3<T> &r, T s) {
 #pragma unroll
@@ -337,13 +391,21 @@ __device__ __forceinline__ void m3_scale(M3<T> &r, T s) {
 // Link load / store
 // --------------------------------------------------------------------------
 
-// Vector planes of one direction mu (element offset mu * NC * P):
-//   float, 18 reals : 4 planes of float4 (complex entries 0-1, 2-3, 4-5, 6-7)
-//                     then 1 plane of float2 (entry 8)
-//   float, 12 reals : 3 planes of float4 (entries 0-1, 2-3, 4-5); row 2 rebuilt
-//   double, 18 reals: 9 planes of double2 (one complex entry each)
-// A plane holding w reals per site starts at (reals before it) * P and site i
-// sits at w * i inside it, so every load is one aligned 8- or 16-byte vector.
+// Links of one direction mu start at element mu * NC * P and come in blocks
+// of 16 consecutive plane positions (P is a multiple of 256).  Inside block
+// b = i / 16 each vector chunk of the 16 links is contiguous:
+//   float, 18 reals : 4 float4 chunks (complex entries 0-1, 2-3, 4-5, 6-7),
+//                     then 1 float2 chunk (entry 8): 1152-byte blocks
+//   float, 12 reals : 3 float4 chunks (entries 0-1, 2-3, 4-5): 768 bytes; row 2 rebuilt
+//   double, 18 reals: 9 double2 chunks (one complex entry each): 2304 bytes
+// so chunk c of the link at position i is one aligned vector at block offset
+// (chunk bytes x 16 before c) + (i mod 16) x (chunk bytes): the chunks of a link
+// sit at compile-time offsets from its first one (a single address per link),
+// and every float4 chunk run of a block starts on a 128-byte line.
+template <int NC>
+__device__ __forceinline__ int blk_off4(int i) { return 4 * i + (i >> 4) * (16 * NC - 64); }  // float4 chunk 0
+__device__ __forceinline__ int blk_off2(int i) { return 2 * i + (i >> 4) * (16 * 18 - 32) + 256; }  // float2 chunk
+__device__ __forceinline__ int blk_offd(int i) { return 2 * i + (i >> 4) * (16 * 18 - 32); }  // double2 chunk 0
 // row 2 = conj(row 0 x row 1): the third row of an SU(3) matrix from the first two,
 // each component one chain of fused multiply-adds (four operations)
 template <class T>
@@ -365,19 +427,21 @@ __device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P,
     const T *base = U + (long long)mu * NC * P;
     M3<T> m;
     if constexpr (sizeof(T) == 4) {
+        const float *b0 = base + blk_off4<NC>(i);
 #pragma unroll
         for (int q = 0; q < NC / 4; ++q) {
-            float4 v = __ldg(reinterpret_cast<const float4 *>(base + 4 * q * P) + i);
+            float4 v = __ldg(reinterpret_cast<const float4 *>(b0 + 64 * q));
             m.re[2 * q] = v.x; m.im[2 * q] = v.y; m.re[2 * q + 1] = v.z; m.im[2 * q + 1] = v.w;
         }
         if (NC == 18) {
-            float2 v = __ldg(reinterpret_cast<const float2 *>(base + 16 * P) + i);
+            float2 v = __ldg(reinterpret_cast<const float2 *>(base + blk_off2(i)));
             m.re[8] = v.x; m.im[8] = v.y;
         }
     } else {
+        const T *b0 = base + blk_offd(i);
 #pragma unroll
         for (int e = 0; e < NC / 2; ++e) {
-            double2 v = __ldg(reinterpret_cast<const double2 *>(base + 2 * e * P) + i);
+            double2 v = __ldg(reinterpret_cast<const double2 *>(b0 + 32 * e));
             m.re[e] = v.x; m.im[e] = v.y;
         }
     }
@@ -389,15 +453,17 @@ template <class T, int NC>
 __device__ __forceinline__ void store_link(T *__restrict__ U, long long P, int mu, int i, const M3<T> &m) {
     T *base = U + (long long)mu * NC * P;
     if constexpr (sizeof(T) == 4) {
+        float *b0 = base + blk_off4<NC>(i);
 #pragma unroll
         for (int q = 0; q < NC / 4; ++q)
-            reinterpret_cast<float4 *>(base + 4 * q * P)[i] =
+            *reinterpret_cast<float4 *>(b0 + 64 * q) =
                 make_float4(m.re[2 * q], m.im[2 * q], m.re[2 * q + 1], m.im[2 * q + 1]);
-        if (NC == 18) reinterpret_cast<float2 *>(base + 16 * P)[i] = make_float2(m.re[8], m.im[8]);
+        if (NC == 18) *reinterpret_cast<float2 *>(base + blk_off2(i)) = make_float2(m.re[8], m.im[8]);
     } else {
+        T *b0 = base + blk_offd(i);
 #pragma unroll
         for (int e = 0; e < NC / 2; ++e)
-            reinterpret_cast<double2 *>(base + 2 * e * P)[i] = make_double2(m.re[e], m.im[e]);
+            *reinterpret_cast<double2 *>(b0 + 32 * e) = make_double2(m.re[e], m.im[e]);
     }
 }
 

@@ -455,14 +455,15 @@ struct LinkRing {
 template <int NC, int SLOT>
 __device__ __forceinline__ void ring_fetch(const LinkRing<NC> &R, const float *base, long long P, int i) {
     constexpr int NQ = NC / 4;
+    const float *b0 = base + blk_off4<NC>(i);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        const float4 *src = reinterpret_cast<const float4 *>(base + 4 * q * P) + i;
+        const float4 *src = reinterpret_cast<const float4 *>(b0 + 64 * q);
         const uint32_t dst = R.a4 + (uint32_t)((SLOT * NQ + q) * VS_RING_THREADS * 16);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
     }
     if (NC == 18) {
-        const float2 *src = reinterpret_cast<const float2 *>(base + 16 * P) + i;
+        const float2 *src = reinterpret_cast<const float2 *>(base + blk_off2(i));
         const uint32_t dst = R.a2 + (uint32_t)(SLOT * VS_RING_THREADS * 8);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
     }
@@ -475,9 +476,10 @@ __device__ __forceinline__ void ring_fetch_if(const LinkRing<NC> &R, const float
                                               bool on) {
     constexpr int NQ = NC / 4;
     const int pr = on ? 1 : 0;
+    const float *b0 = base + blk_off4<NC>(i);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        const float4 *src = reinterpret_cast<const float4 *>(base + 4 * q * P) + i;
+        const float4 *src = reinterpret_cast<const float4 *>(b0 + 64 * q);
         const uint32_t dst = R.a4 + (uint32_t)((SLOT * NQ + q) * VS_RING_THREADS * 16);
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
@@ -485,7 +487,7 @@ __device__ __forceinline__ void ring_fetch_if(const LinkRing<NC> &R, const float
             : "memory");
     }
     if (NC == 18) {
-        const float2 *src = reinterpret_cast<const float2 *>(base + 16 * P) + i;
+        const float2 *src = reinterpret_cast<const float2 *>(base + blk_off2(i));
         const uint32_t dst = R.a2 + (uint32_t)(SLOT * VS_RING_THREADS * 8);
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
@@ -613,8 +615,7 @@ __device__ __forceinline__ void fused_unit(const LinkRing<NC> &R, M3<float> &Fac
         u_refill<NC, S, 5>(R, Umu, Unu, Un, P, A, An, last);
         m3_mul_2r(Y, X, E);
         rebuild_row2(Y);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) { Facc.re[k] += Y.re[k]; Facc.im[k] += Y.im[k]; }
+        m3_acc_f32(Facc, Y);
     }
     {   // A T, T = T0 T1 T2
         const M3<float> T0 = ring_take6<NC, (S < 0), 0, false>(R);
@@ -630,12 +631,7 @@ __device__ __forceinline__ void fused_unit(const LinkRing<NC> &R, M3<float> &Fac
         rebuild_row2(X);
     }
     rebuild_row2(AB);
-    // Yc = c1 (W1 + A T) + c0 A B
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        Y.re[k] = fmaf(c0, AB.re[k], c1 * (W1.re[k] + X.re[k]));
-        Y.im[k] = fmaf(c0, AB.im[k], c1 * (W1.im[k] + X.im[k]));
-    }
+    m3_lin3_f32(Y, c0, AB, c1, W1, X);   // Yc = c1 (W1 + A T) + c0 A B
     const M3<float> C = ring_take6<NC, (S > 0), 3>(R);
     u_refill<NC, S, 9>(R, Umu, Unu, Un, P, A, An, last);
     m3_madd(sig, Y, C);
