@@ -157,3 +157,56 @@ def test_served_job_on_a_padded_lattice_equals_the_direct_run(ctx):
     U = vs.vs_read_field(f)
     vs.vs_field_destroy(f)
     assert np.array_equal(U, out)
+
+
+class _DeviceArray:
+    """A raw device buffer of the library, seen by torch through the CUDA
+    array interface (no copy)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": (n,), "typestr": typestr,
+                                         "version": 3}
+
+
+@pytest.mark.parametrize("dims", [(8, 4, 4, 8)] + PADDED)
+@pytest.mark.parametrize("mode", ["fp32_18", "fp32_12", "fp64_18"])
+def test_device_links_follow_the_documented_blocked_layout(ctx, dims, mode):
+    """vs_field_desc documents the device layout for callers that read the
+    links in place: direction mu at element mu NC P, blocks of 16 plane
+    positions, each vector chunk of a block contiguous.  Every stored real of
+    every link sits where that description puts it."""
+    torch = pytest.importorskip("torch")
+    precision = vs.VS_FP64 if mode == "fp64_18" else vs.VS_FP32
+    storage = vs.VS_LINK12 if mode == "fp32_12" else vs.VS_LINK18
+    U = synth.haar_field(dims, 31)
+    f = vs.vs_field_create(ctx, dims, precision, storage)
+    try:
+        vs.vs_load_field(f, links=U)
+        Ur = vs.vs_read_field(f)
+        vs.vs_synchronize(f)
+        d = vs.vs_field_describe(f)
+        P, NC = d["plane_stride"], d["n_components"]
+        assert P % 256 == 0
+        typestr = "<f8" if precision == vs.VS_FP64 else "<f4"
+        raw = torch.as_tensor(_DeviceArray(d["links"], 4 * NC * P, typestr), device="cuda").cpu().numpy()
+    finally:
+        vs.vs_field_destroy(f)
+    V = int(np.prod(dims))
+    Ur = Ur.reshape(4, V, 3, 3)
+    Lx, Ly, Lz, Lt = dims
+    for s in range(V):
+        x = (s % Lx, (s // Lx) % Ly, (s // (Lx * Ly)) % Lz, s // (Lx * Ly * Lz))
+        i = vs.vs_layout_index(dims, x)
+        b, k = divmod(i, 16)
+        for mu in range(4):
+            base = mu * NC * P + b * 16 * NC
+            ent = Ur[mu, s].reshape(9)
+            n_ent = 6 if NC == 12 else 9
+            for e in range(n_ent):
+                if precision == vs.VS_FP64:
+                    off = base + 32 * e + 2 * k
+                elif e < 8:
+                    off = base + 64 * (e // 2) + 4 * k + 2 * (e % 2)
+                else:
+                    off = base + 256 + 2 * k
+                assert raw[off] == ent[e].real and raw[off + 1] == ent[e].imag, (mu, x, e)
