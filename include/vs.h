@@ -382,20 +382,22 @@ typedef struct {
     int8_t *labels;                /* device: [4][plane_stride] reference labels */
     void *stream;
     void *gauge;                   /* device: the random gauge transformation G of vs_gauge_transform
-                                      (18 reals per site in the field precision, one plane group as
-                                      for direction 0 of the links), or NULL in the original gauge */
+                                      (18 reals per site in the field precision, laid out as
+                                      direction 0 of 18-real links), or NULL in the original gauge */
 } vs_field_desc;
 
-/* Device layout of a field.  Within a component plane the sites follow the
- * lexicographic rows (y, z, t), and inside each x-row the sites are grouped
- * by x mod 4: position row * 4Qp + (x mod 4) * Qp + x/4 (see vs_layout_index),
- * where Qp = Lx/4, except Qp = 8 when Lx/4 is 5, 6 or 7: a group of one
- * colour class's sites then fills one 128-byte line of a float4 plane instead
- * of straddling two, and the positions Lx/4 .. 7 of each group hold no link
- * (plane_stride = 4 Qp Ly Lz Lt). */
+/* Device layout of a field.  Site positions (the index of the labels and of
+ * the link blocks) follow the lexicographic rows (y, z, t), and inside each
+ * x-row the sites are grouped by x mod 4: position row * 4Qp + (x mod 4) * Qp
+ * + x/4 (see vs_layout_index), where Qp = Lx/4, except Qp = 8 when Lx/4 is 5,
+ * 6 or 7: a group of one colour class's sites then fills one 128-byte line
+ * of a float4 chunk run instead of straddling two, and the positions
+ * Lx/4 .. 7 of each group hold no link (plane_stride = 4 Qp Ly Lz Lt, a
+ * multiple of 256).  The links of position i are in block i / 16 of their
+ * direction, element i mod 16 of each of its chunks (vs_field_desc.links). */
 vs_status vs_field_describe(const vs_field *f, vs_field_desc *out);
 
-/* Position of site (x,y,z,t) inside a component plane (layout above). */
+/* Position of site (x,y,z,t) in the device layout (above). */
 int64_t vs_layout_index(const int32_t dims[4], const int32_t x[4]);
 
 /* Number of kernels the library has launched directly in this process (CUDA

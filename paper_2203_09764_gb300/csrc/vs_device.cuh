@@ -1,17 +1,18 @@
 // vs_device.cuh -- device-side SU(3) algebra, lattice geometry and field layout.
 //
-// Field layout in HBM (structure of vector planes):
+// Field layout in HBM:
 //   links of direction mu: NC reals per site (NC = 18: row-major 3x3 as
 //   re,im pairs; NC = 12: rows 0 and 1 only, row 2 rebuilt as
-//   conj(row0 x row1) on load), split into planes of float4 / float2 /
-//   double2 vectors (see load_link); i = site position in a plane.
+//   conj(row0 x row1) on load) at element mu NC P, in blocks of 16 site
+//   positions holding each float4 / float2 / double2 vector chunk of their
+//   16 links contiguously (see load_link); i = site position.
 //   Site position: rows (y, z, t) in lexicographic order, and inside each
 //   x-row the sites grouped by x mod 4: i = row*4Qp + (x & 3)*Qp + (x >> 2),
 //   Qp = Lx/4, or 8 when Lx/4 is 5, 6 or 7 (the group then ends in unused
 //   positions).  For a colour class of the annealed schedule the updated
 //   sites of one row form contiguous runs of Lx/4, so a warp's loads of any
-//   plane are whole 32-byte sectors; with the padding a run of 5-7 sites
-//   (80-112 bytes of a float4 plane) never straddles a 128-byte line.
+//   chunk are whole 32-byte sectors; with the padding a run of 5-7 sites
+//   (80-112 bytes of a float4 chunk) never straddles a 128-byte line.
 //   labels[mu][i]    int8 reference Z(3) label of link (mu, i).
 #pragma once
 
@@ -26,7 +27,7 @@ struct Geo {
     int Qp;         // positions of that group in the layout (Q, or 8 for Q = 5, 6, 7)
     int Lxp;        // positions of an x-row: 4 Qp
     int V;          // sites
-    long long P;    // plane stride in sites (positions): Lxp Ly Lz Lt >= V
+    long long P;    // site positions per direction (plane stride): Lxp Ly Lz Lt >= V
 };
 
 // The geometry of extents dims (each a positive multiple of 4).

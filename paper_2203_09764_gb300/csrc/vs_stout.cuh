@@ -450,8 +450,8 @@ struct LinkRing {
     uint32_t a4, a2;    // the same as shared-window addresses
 };
 
-// Start the copy of the link at plane position i of the direction whose
-// planes begin at base into slot SLOT, as one commit group.
+// Start the copy of the link at site position i of the direction whose
+// links begin at base into slot SLOT, as one commit group.
 template <int NC, int SLOT>
 __device__ __forceinline__ void ring_fetch(const LinkRing<NC> &R, const float *base, long long P, int i) {
     constexpr int NQ = NC / 4;
