@@ -274,7 +274,28 @@ __device__ __forceinline__ M3<T> exp_iH(T h00, T h11, T h22, T h01r, T h01i, T h
     H.re[1] = h01r; H.im[1] = h01i; H.re[3] = h01r; H.im[3] = -h01i;
     H.re[2] = h02r; H.im[2] = h02i; H.re[6] = h02r; H.im[6] = -h02i;
     H.re[5] = h12r; H.im[5] = h12i; H.re[7] = h12r; H.im[7] = -h12i;
-    M3<T> H2 = m3_mul(H, H);
+    // H^2 is Hermitian: its diagonal (real) and upper entries, the lower ones
+    // by conjugation (a third of the operations of a general product)
+    M3<T> H2;
+    {
+        const T a01 = h01r * h01r + h01i * h01i, a02 = h02r * h02r + h02i * h02i, a12 = h12r * h12r + h12i * h12i;
+        H2.re[0] = fma(h00, h00, a01 + a02); H2.im[0] = 0;
+        H2.re[4] = fma(h11, h11, a01 + a12); H2.im[4] = 0;
+        H2.re[8] = fma(h22, h22, a02 + a12); H2.im[8] = 0;
+        const T s01 = h00 + h11, s02 = h00 + h22, s12 = h11 + h22;
+        // (0,1): h01 (h00 + h11) + h02 conj(h12)
+        H2.re[1] = fma(h01r, s01, fma(h02r, h12r, h02i * h12i));
+        H2.im[1] = fma(h01i, s01, fma(h02i, h12r, -(h02r * h12i)));
+        // (0,2): h02 (h00 + h22) + h01 h12
+        H2.re[2] = fma(h02r, s02, fma(h01r, h12r, -(h01i * h12i)));
+        H2.im[2] = fma(h02i, s02, fma(h01r, h12i, h01i * h12r));
+        // (1,2): h12 (h11 + h22) + conj(h01) h02
+        H2.re[5] = fma(h12r, s12, fma(h01r, h02r, h01i * h02i));
+        H2.im[5] = fma(h12i, s12, fma(h01r, h02i, -(h01i * h02r)));
+        H2.re[3] = H2.re[1]; H2.im[3] = -H2.im[1];
+        H2.re[6] = H2.re[2]; H2.im[6] = -H2.im[2];
+        H2.re[7] = H2.re[5]; H2.im[7] = -H2.im[5];
+    }
     M3<T> Mx;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
