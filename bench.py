@@ -402,8 +402,10 @@ def vortex_diagnostics(vs, ctx, stream, labels_dev, args):
     """The workload's sweeps with and without vortex preservation (Sec. VI),
     per-sweep statistics from the kernels: candidates whose Z(3) label differs
     from the original (without VP: the label differences after the sweep, the
-    n_diff of the paper's tables), candidates inside the FP32 rounding band of a
-    sector edge, the smallest candidate margin, and the action."""
+    n_diff of the paper's tables), candidates inside the rounding band of a sector
+    edge (with VP the FP32 candidates inside the FP32 band are decided again in
+    FP64, and those left within the band of the FP32 link storage are counted),
+    the smallest candidate margin, and the action."""
     out = {}
     marks = [k for k in (1, 2, 5, 10, 20, 50, 100, 200, 300) if k <= args.sweeps]
     for vp in (True, False):
@@ -419,6 +421,7 @@ def vortex_diagnostics(vs, ctx, stream, labels_dev, args):
             "action_at_sweep": {str(k): st[k - 1]["action"] for k in marks},
             "min_margin_at_sweep": {str(k): st[k - 1]["min_margin"] for k in marks},
             "n_undecidable_total": int(sum(s["n_undecidable"] for s in st)),
+            "n_fp64_redecided_total": int(sum(s["n_fp64_redecided"] for s in st)),
             "n_fp64_exp_total": int(sum(s["n_fp64_exp"] for s in st)),
             "after_last_sweep": {"n_label_diff": chk["n_label_diff"], "n_charge_diff": chk["n_charge_diff"]}}
     out["what"] = ("%d sweeps of the workload (FP32 18-real) with per-sweep statistics; with VP the "

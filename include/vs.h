@@ -133,6 +133,15 @@ typedef struct {
     const double *rho_per_sweep;  /* host [n_sweeps] step sizes, or NULL for constant rho */
     int32_t reunit_every;         /* FP32: re-unitarise (Gram-Schmidt in FP32) every k sweeps; 0 = never */
     int32_t action_every;         /* record <S> in stats every k sweeps; 0 = never */
+    int32_t fp64_redecide;        /* FP32 with vortex preservation: a candidate whose FP32 trace lies within
+                                     the FP32 band of a sector edge (n_undecidable below) is left unwritten
+                                     by its class launch and decided again in FP64 from the same stored
+                                     links before the next class (1), or decided in FP32 (0, the default
+                                     when sched is NULL).  The FP64 pass sits between dependent class
+                                     launches on GB300's FP64 pipe (~60 us per candidate): with ~80 such
+                                     candidates per sweep at 32^3x64 a sweep takes 2.8x as long.  A
+                                     candidate accepted in FP64 whose FP32-rounded link would carry
+                                     another label keeps the old link. */
 } vs_anneal;
 
 typedef struct {
@@ -148,13 +157,17 @@ typedef struct {
     int64_t n_label_diff;         /* candidates whose Z(3) label (Sec. I) differs from the reference label;
                                      with vortex preservation these are the rejections, without it the
                                      label differences after the sweep */
-    int64_t n_undecidable;        /* candidates whose trace lies within the precision's rounding band of a
-                                     sector edge (FP32: 2e-6, FP64: 1e-12, in trace units), where another
-                                     rounding of the same arithmetic could decide the test differently;
-                                     outside it the decision equals that of exact arithmetic on the
-                                     stored links */
+    int64_t n_undecidable;        /* candidates whose trace lies within the rounding band of a sector
+                                     edge (in trace units: FP32 arithmetic 2e-6, FP32 candidates decided
+                                     again in FP64 1e-6, FP64 1e-12), where another rounding could
+                                     decide the test differently; outside it the decision equals that
+                                     of exact arithmetic on the stored links (FP32 arithmetic: on the
+                                     stored links up to that band) */
     double min_margin;            /* smallest angular distance of a candidate's arg Tr from a sector edge
                                      (radians) */
+    int64_t n_fp64_redecided;     /* FP32 candidates decided in FP64 (vs_anneal.fp64_redecide); their
+                                     undecidable band is then that of the FP32 storage of the links
+                                     (1e-6), not of FP32 arithmetic */
 } vs_sweep_stats;
 
 /* n_sweeps of stout smoothing, Eqs. (stout)/(generator), with

@@ -125,7 +125,7 @@ uint64_t vs::field_footprint(const int32_t dims[4], int32_t precision, int32_t s
     const long long P = make_geo(dims).P;   // plane stride, with the layout's unused positions
     int nc = storage == VS_LINK12 ? 12 : 18;
     uint64_t links = (uint64_t)4 * nc * P * (precision == VS_FP64 ? 8 : 4);
-    return links + 8ull * P + 1216 * 8 + 4096;
+    return links + 8ull * P + 1216 * 8 + 4096 + (precision == VS_FP32 ? kDeferCap * sizeof(int) : 0);
 }
 
 extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t precision, int32_t storage,
@@ -158,7 +158,8 @@ extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t p
     f->ref = (int8_t *)dev_alloc(c, 4 * (size_t)f->g.P);
     f->cur = (int8_t *)dev_alloc(c, 4 * (size_t)f->g.P);
     f->partials = (double *)dev_alloc(c, 1216 * sizeof(double) + 4096);
-    if (!f->U || !f->ref || !f->cur || !f->partials) {
+    if (precision == VS_FP32) f->defer_idx = (int *)dev_alloc(c, kDeferCap * sizeof(int));
+    if (!f->U || !f->ref || !f->cur || !f->partials || (precision == VS_FP32 && !f->defer_idx)) {
         vs_field_destroy(f);
         return fail(VS_ENOMEM, "vs_field_create: device allocation of %zu bytes failed", field_bytes(f));
     }
@@ -166,6 +167,12 @@ extern "C" vs_status vs_field_create(vs_ctx *c, const int32_t dims[4], int32_t p
     f->d_result = f->partials + 1216;
     f->d_counts = (unsigned long long *)(f->d_result + 1);      // 8 slots
     f->d_sweep = f->d_counts + 8;                               // kSweepSlots slots
+    f->defer_n = (unsigned *)(f->d_sweep + kSweepSlots);        // 2 counters
+    cudaError_t e = cudaMemsetAsync(f->defer_n, 0, 2 * sizeof(unsigned), f->stream);
+    if (e != cudaSuccess) {
+        vs_field_destroy(f);
+        return cuda_fail(e, "vs_field_create");
+    }
     *out = f;
     return VS_OK;
 }
@@ -179,6 +186,7 @@ extern "C" void vs_field_destroy(vs_field *f) {
     dev_free(f->ctx, f->cur);
     dev_free(f->ctx, f->G);
     dev_free(f->ctx, f->partials);
+    dev_free(f->ctx, f->defer_idx);
     dev_free(f->ctx, f->scratch);
     dev_free(f->ctx, f->flowS);
     dev_free(f->ctx, f->sweep_counts);
@@ -486,13 +494,14 @@ static double margin_of_sine_bits(unsigned long long bits) {
 static void fill_vp_stats(vs_sweep_stats &o, const unsigned long long *c) {
     o.n_label_diff = (int64_t)c[kCntLabelDiff];
     o.n_undecidable = (int64_t)c[kCntUndecidable];
+    o.n_fp64_redecided = (int64_t)c[kCntRedecided];
     o.min_margin = margin_of_sine_bits(c[kCntMarginSine]);
 }
 
 cudaError_t vs::init_sweep_counters(unsigned long long *c, int n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t pitch = kSweepSlots * sizeof(unsigned long long);
-    cudaError_t e = cudaMemset2DAsync(c, pitch, 0, kCntMarginSine * sizeof(unsigned long long), n, st);
+    cudaError_t e = cudaMemset2DAsync(c, pitch, 0, pitch, n, st);
     if (e == cudaSuccess)
         e = cudaMemset2DAsync(c + kCntMarginSine, pitch, 0x7f, sizeof(unsigned long long), n, st);
     return e;
@@ -515,7 +524,9 @@ static vs_status check_smooth_params(double rho, double eps, double u0) {
     return VS_OK;
 }
 
-static SubsweepParams make_params(vs_field *f, double rho, double eps, double u0, int vp) {
+// redecide: FP32 with vortex preservation, candidates within the FP32 band of
+// a sector edge are decided again in FP64 (k_redecide).
+static SubsweepParams make_params(vs_field *f, double rho, double eps, double u0, int vp, bool redecide) {
     SubsweepParams p;
     memset(&p, 0, sizeof p);
     p.g = f->g;
@@ -530,6 +541,12 @@ static SubsweepParams make_params(vs_field *f, double rho, double eps, double u0
     p.c0_f = (float)p.c0;
     p.c1_f = (float)p.c1;
     p.vp = vp ? 1 : 0;
+    if (redecide && vp && f->prec == VS_FP32 && f->defer_idx) {
+        p.defer_idx = f->defer_idx;
+        p.defer_n = f->defer_n;
+        p.defer_done = f->defer_n + 1;
+        p.defer_cap = kDeferCap;
+    }
     return p;
 }
 
@@ -541,7 +558,7 @@ extern "C" vs_status vs_subsweep(vs_field *f, int32_t mu, int32_t colour, double
     vs_status st = check_smooth_params(rho, eps, u0);
     if (st) return st;
     CK(cudaSetDevice(f->ctx->opt.device));
-    SubsweepParams p = make_params(f, rho, eps, u0, vp);
+    SubsweepParams p = make_params(f, rho, eps, u0, vp, false);
     p.colour = colour;
     p.n_threads = f->g.V / 4;
     p.counters = f->d_sweep;
@@ -620,7 +637,7 @@ vs_status vs::smooth_enqueue(vs_field *f, int32_t n_sweeps, double rho, double e
     for (int s = 0; s < n_sweeps; ++s) {
         NvtxRange range("vs stout sweep");
         const double r = a.rho_per_sweep ? a.rho_per_sweep[s] : rho;
-        SubsweepParams p = make_params(f, r, eps, u0, vp);
+        SubsweepParams p = make_params(f, r, eps, u0, vp, a.fp64_redecide != 0);
         p.counters = fixed_counters ? fixed_counters : (want_stats ? f->sweep_counts + kSweepSlots * s : nullptr);
         if (f->profiling) CK(cudaEventRecord(f->events[2 * s], f->stream));
         if (a.kind == VS_ANNEALED) {

@@ -46,6 +46,8 @@ struct vs_field {
     double *d_result = nullptr;
     unsigned long long *d_counts = nullptr;
     unsigned long long *d_sweep = nullptr;  // kSweepSlots counters of vs_subsweep and served jobs
+    int *defer_idx = nullptr;       // FP32: positions left by a class launch to k_redecide [kDeferCap]
+    unsigned *defer_n = nullptr;    // [0] entries appended, [1] k_redecide blocks done
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     void *flowS = nullptr;          // Runge-Kutta exponent H_S, 9 reals per link

@@ -81,6 +81,19 @@ __device__ __forceinline__ Pt site_of_index(const Geo &g, int i) {
     return p;
 }
 
+// The site at layout position i (the inverse of sidx on used positions).
+__device__ __forceinline__ Pt site_of_pos(const Geo &g, int i) {
+    Pt p;
+    const int r = i % g.Lxp;
+    int row = i / g.Lxp;
+    p.x0 = 4 * (r % g.Qp) + r / g.Qp;
+    p.x1 = row % g.L[1];
+    row /= g.L[1];
+    p.x2 = row % g.L[2];
+    p.x3 = row / g.L[2];
+    return p;
+}
+
 __device__ __forceinline__ Pt site_of_lex(const Geo &g, int s) {
     Pt p;
     p.x0 = s % g.L[0]; s /= g.L[0];
@@ -423,8 +436,9 @@ __device__ __forceinline__ void rebuild_row2(M3<T> &m) {
     }
 }
 
+// The stored reals of a link (row 2 of 12-real links not yet rebuilt).
 template <class T, int NC>
-__device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P, int mu, int i) {
+__device__ __forceinline__ M3<T> load_link_raw(const T *__restrict__ U, long long P, int mu, int i) {
     const T *base = U + (long long)mu * NC * P;
     M3<T> m;
     if constexpr (sizeof(T) == 4) {
@@ -446,8 +460,35 @@ __device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P,
             m.re[e] = v.x; m.im[e] = v.y;
         }
     }
+    return m;
+}
+
+template <class T, int NC>
+__device__ __forceinline__ M3<T> load_link(const T *__restrict__ U, long long P, int mu, int i) {
+    M3<T> m = load_link_raw<T, NC>(U, P, mu, i);
     if (NC == 12) rebuild_row2(m);
     return m;
+}
+
+template <class T, class S>
+__device__ __forceinline__ M3<T> m3_cast(const M3<S> &a) {
+    M3<T> r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { r.re[k] = T(a.re[k]); r.im[k] = T(a.im[k]); }
+    return r;
+}
+
+// A link stored in precision S as an M3<T>: for FP32 storage read in FP64,
+// the stored reals exactly, and row 2 of 12-real links rebuilt in FP64.
+template <class T, int NC, class S>
+__device__ __forceinline__ M3<T> load_link_as(const S *__restrict__ U, long long P, int mu, int i) {
+    if constexpr (sizeof(T) == sizeof(S)) {
+        return load_link<T, NC>(U, P, mu, i);
+    } else {
+        M3<T> m = m3_cast<T>(load_link_raw<S, NC>(U, P, mu, i));
+        if (NC == 12) rebuild_row2(m);
+        return m;
+    }
 }
 
 template <class T, int NC>
@@ -512,15 +553,15 @@ __device__ __forceinline__ T edge_sine(T a, T b, T d) {
 // gauge (G == nullptr); after a random gauge transformation G,
 // Tr[G^dag(x) U G(x+mu)] = sum_jk U_jk (G(x+mu) G^dag(x))_kj.  G is stored as
 // 18 reals per site in the link layout, plane position i.
-template <class T>
-__device__ __forceinline__ void vp_trace(const T *__restrict__ G, long long P, int i_x, int i_xmu,
+template <class T, class S = T>
+__device__ __forceinline__ void vp_trace(const S *__restrict__ G, long long P, int i_x, int i_xmu,
                                          const M3<T> &u, T &a, T &b) {
     if (!G) {
         a = u.re[0] + u.re[4] + u.re[8];
         b = u.im[0] + u.im[4] + u.im[8];
         return;
     }
-    const M3<T> gx = load_link<T, 18>(G, P, 0, i_x), gy = load_link<T, 18>(G, P, 0, i_xmu);
+    const M3<T> gx = load_link_as<T, 18>(G, P, 0, i_x), gy = load_link_as<T, 18>(G, P, 0, i_xmu);
     T sr = T(0), si = T(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j)

@@ -20,6 +20,13 @@ struct SubsweepParams {
     float rho_f, c0_f, c1_f;   // the same, rounded once on the host for the FP32 kernels
     int vp;
     unsigned long long *counters;  // kSweepSlots counters of the sweep (kCnt*), or null
+    // FP32 with vortex preservation and vs_anneal.fp64_redecide: candidates
+    // within the FP32 band of a sector edge are left unwritten and listed here
+    // for k_redecide (FP64); null: decided in FP32 and counted as undecidable
+    int *defer_idx;       // [defer_cap] layout positions
+    unsigned *defer_n;    // entries appended by the class launch (may exceed defer_cap)
+    unsigned *defer_done; // blocks of k_redecide that have finished (reset by the last)
+    int defer_cap;
 };
 
 // Counter slots of one sweep, filled by the colour-class kernels of the
@@ -33,9 +40,15 @@ enum {
     kCntLabelDiff = 2,    // candidates whose Z(3) label differs from the reference
     kCntUndecidable = 3,  // candidates whose trace lies within the precision's error band of an edge
     kCntMarginSine = 4,
+    kCntRedecided = 5,    // FP32 candidates re-decided in FP64 (k_redecide)
     kSweepSlots = 8
 };
 constexpr unsigned long long kMarginInit = 0x7f7f7f7f7f7f7f7full;   // a double of about 1.4e306
+
+// Capacity of a field's list of FP32 candidates left to k_redecide per class
+// launch (a launch that defers more decides the rest in FP32, counted as
+// undecidable).
+constexpr int kDeferCap = 16384;
 
 // process-wide count of direct kernel launches
 void count_launches(int n);

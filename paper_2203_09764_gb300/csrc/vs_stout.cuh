@@ -56,9 +56,10 @@ __device__ __forceinline__ int shift_delta(const Geo &g, const Pt &x, int d, int
 }
 
 // Link of direction d at plane position i, daggered when dag is true.
-template <class T, int NC>
-__device__ __forceinline__ M3<T> link_at(const Geo &g, const T *__restrict__ U, int d, int i, bool dag) {
-    M3<T> m = load_link<T, NC>(U, g.P, d, i);
+// St: the storage precision (FP32 links read in FP64 by the re-decision kernel).
+template <class T, int NC, class St = T>
+__device__ __forceinline__ M3<T> link_at(const Geo &g, const St *__restrict__ U, int d, int i, bool dag) {
+    M3<T> m = load_link_as<T, NC>(U, g.P, d, i);
     return dag ? m3_dag(m) : m;
 }
 
@@ -94,28 +95,28 @@ __device__ __forceinline__ void around_nu(const Geo &g, const Pt &x, int nu, boo
 }
 
 // Path step along s*nu from site x + a nu + b mu.
-template <class T, int NC>
-__device__ __forceinline__ M3<T> step_fwd(const Geo &g, const T *__restrict__ U, const Around &S, int nu,
+template <class T, int NC, class St = T>
+__device__ __forceinline__ M3<T> step_fwd(const Geo &g, const St *__restrict__ U, const Around &S, int nu,
                                           int s, int a, int b) {
     return s > 0 ? link_at<T, NC>(g, U, nu, around_pos(S, a, b), false)
                  : link_at<T, NC>(g, U, nu, around_pos(S, a - 1, b), true);
 }
 
 // Path step along -s*nu from site x + a nu + b mu.
-template <class T, int NC>
-__device__ __forceinline__ M3<T> step_back(const Geo &g, const T *__restrict__ U, const Around &S, int nu,
+template <class T, int NC, class St = T>
+__device__ __forceinline__ M3<T> step_back(const Geo &g, const St *__restrict__ U, const Around &S, int nu,
                                            int s, int a, int b) {
     return s > 0 ? link_at<T, NC>(g, U, nu, around_pos(S, a - 1, b), true)
                  : link_at<T, NC>(g, U, nu, around_pos(S, a, b), false);
 }
 
-template <class T, int NC, int MU>
-__device__ __forceinline__ M3<T> link_mu(const Geo &g, const T *__restrict__ U, const Around &S, int a, int b) {
+template <class T, int NC, int MU, class St = T>
+__device__ __forceinline__ M3<T> link_mu(const Geo &g, const St *__restrict__ U, const Around &S, int a, int b) {
     return link_at<T, NC>(g, U, MU, around_pos(S, a, b), false);
 }
 
-template <class T, int NC, bool RECT, int MU>
-__device__ __forceinline__ M3<T> staple_sum(const Geo &g, const T *__restrict__ U, Pt x, T c0, T c1) {
+template <class T, int NC, bool RECT, int MU, class St = T>
+__device__ __forceinline__ M3<T> staple_sum(const Geo &g, const St *__restrict__ U, Pt x, T c0, T c1) {
     Around S;
     S.i0 = sidx(g, x);
     S.dmm1 = shift_delta(g, x, MU, -1);
@@ -367,12 +368,13 @@ template <> struct EdgeBand<double> { static __device__ __forceinline__ double v
 // The candidate's label against the reference (Sec. VI), its distance from
 // the nearest sector edge (Sec. I Eq. centre_element) and the margin sine.
 template <class T>
-__device__ __forceinline__ void vp_decide(bool vp, bool want_sine, int ref, T tr_re, T tr_im, Update<T> &u) {
+__device__ __forceinline__ void vp_decide(bool vp, bool want_sine, int ref, T tr_re, T tr_im, Update<T> &u,
+                                          T band = EdgeBand<T>::v()) {
     const int lab = z3_label<T>(tr_re, tr_im);
     const T dist = edge_distance<T>(tr_re, tr_im, lab);
     u.reject = vp && lab != ref;
     u.labdiff = lab != ref;
-    u.undec = dist < EdgeBand<T>::v();
+    u.undec = dist < band;
     if (want_sine) u.sine = edge_sine<T>(tr_re, tr_im, dist);
 }
 
@@ -390,6 +392,18 @@ __device__ __forceinline__ void stout_store(const SubsweepParams &a, const Pt &x
     T tr_re, tr_im;
     vp_trace<T>(static_cast<const T *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re, tr_im);
     vp_decide<T>(a.vp, a.counters != nullptr, (int)a.ref[(long long)MU * g.P + i], tr_re, tr_im, u);
+    if constexpr (sizeof(T) == 4) {
+        // within the FP32 band of an edge: leave the link to k_redecide
+        if (a.defer_idx && a.vp && u.undec) {
+            const unsigned slot = atomicAdd(a.defer_n, 1u);
+            if (slot < (unsigned)a.defer_cap) {
+                a.defer_idx[slot] = i;
+                u.reject = u.labdiff = u.undec = false;
+                u.sine = T(2);
+                return;
+            }
+        }
+    }
     // a rejected link keeps its value: nothing to write in place (annealed),
     // the old link into the destination when that is another buffer
     if (!u.reject) store_link<T, NC>(static_cast<T *>(a.U), g.P, MU, i, Un);
@@ -420,6 +434,68 @@ __device__ __forceinline__ void count_update(unsigned long long *c, const Update
         if (lb) atomicAdd(&c[kCntLabelDiff], (unsigned long long)__popc(lb));
         if (ub) atomicAdd(&c[kCntUndecidable], (unsigned long long)__popc(ub));
         if (m < T(2)) atomicMin(&c[kCntMarginSine], (unsigned long long)__double_as_longlong((double)m));
+    }
+}
+
+// Band of a candidate computed in FP64 from FP32-stored links: rounding the
+// links to FP32 moves each entry by up to 6e-8 relative, the candidate's
+// trace by a few 1e-7 (the staple sum adds 48 paths); within this band of an
+// edge the FP32 field itself, not the arithmetic, can decide the test.
+constexpr double kRedecideBand = 1e-6;
+
+// FP64 re-decision of the FP32 candidates a class launch left to it (its
+// FP32 trace within EdgeBand<float> of a sector edge, Sec. VI): the same
+// candidate from the same stored links in FP64 arithmetic, decided, stored
+// (rounded to FP32) if accepted.  No link of a colour class enters the staples
+// of another of the class, so the field the class launch left is this
+// candidate's input.  One lane per listed link; the last block to finish
+// resets the list for the next class launch.
+template <int NC, bool RECT, int MU>
+__global__ void __launch_bounds__(32) k_redecide(SubsweepParams a) {
+    const Geo &g = a.g;
+    const unsigned n = min(*a.defer_n, (unsigned)a.defer_cap);
+    const float *Us = static_cast<const float *>(a.Usrc);
+    for (unsigned k0 = blockIdx.x * 32u; k0 < n; k0 += gridDim.x * 32u) {
+        const unsigned k = k0 + (threadIdx.x & 31u);
+        Update<double> up;
+        if (k < n) {
+            const int i = a.defer_idx[k];
+            const Pt x = site_of_pos(g, i);
+            const M3<double> sig = staple_sum<double, NC, RECT, MU>(g, Us, x, a.c0, a.c1);
+            const M3<double> Ux = load_link_as<double, NC>(Us, g.P, MU, i);
+            M3<double> Un = stout_candidate<double>(sig, Ux, a.rho, up.second);
+            if (NC == 12) rebuild_row2(Un);
+            double tr_re, tr_im;
+            vp_trace<double>(static_cast<const float *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Un, tr_re,
+                             tr_im);
+            const int ref = (int)a.ref[(long long)MU * g.P + i];
+            vp_decide<double>(a.vp, a.counters != nullptr, ref, tr_re, tr_im, up, kRedecideBand);
+            const M3<float> Uf = m3_cast<float>(Un);   // the candidate as stored
+            if (!up.reject) {
+                // vortex preservation holds for the stored FP32 link as every FP32
+                // kernel reads it (12-real: row 2 rebuilt in FP32): a candidate whose
+                // rounding crosses the edge keeps the old link (it lies within the band)
+                M3<float> Uv = Uf;
+                if (NC == 12) rebuild_row2(Uv);
+                float fa, fb;
+                vp_trace<float>(static_cast<const float *>(a.G), g.P, i, a.G ? sidx(g, mv(g, x, MU, 1)) : i, Uv, fa,
+                                fb);
+                if (z3_label<float>(fa, fb) != ref) up.reject = up.labdiff = up.undec = true;
+            }
+            if (!up.reject) store_link<float, NC>(static_cast<float *>(a.U), g.P, MU, i, Uf);
+            else if (a.U != a.Usrc) store_link<float, NC>(static_cast<float *>(a.U), g.P, MU, i, m3_cast<float>(Ux));
+        }
+        count_update<double>(a.counters, up);
+        const unsigned rb = __ballot_sync(0xffffffffu, k < n);
+        if (a.counters && (threadIdx.x & 31u) == 0 && rb)
+            atomicAdd(&a.counters[kCntRedecided], (unsigned long long)__popc(rb));
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        __threadfence();
+        if (atomicAdd(a.defer_done, 1u) == gridDim.x - 1) {
+            *a.defer_n = 0;
+            *a.defer_done = 0;
+        }
     }
 }
 

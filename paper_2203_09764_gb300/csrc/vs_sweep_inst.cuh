@@ -8,6 +8,18 @@
 
 namespace vs {
 
+// FP64 re-decision of the candidates the FP32 class launch just made left to it.
+template <int NC, bool RECT>
+void launch_redecide(int mu, const SubsweepParams &p, cudaStream_t st) {
+    switch (mu) {
+        case 0: k_redecide<NC, RECT, 0><<<16, 32, 0, st>>>(p); break;
+        case 1: k_redecide<NC, RECT, 1><<<16, 32, 0, st>>>(p); break;
+        case 2: k_redecide<NC, RECT, 2><<<16, 32, 0, st>>>(p); break;
+        default: k_redecide<NC, RECT, 3><<<16, 32, 0, st>>>(p); break;
+    }
+    count_launches(1);
+}
+
 template <class T, int NC>
 cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cudaStream_t st) {
     if (p.n_threads <= 0) return cudaSuccess;
@@ -30,6 +42,7 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
                 default: k_subsweep_fused<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
             }
             count_launches(1);
+            if (p.defer_idx) launch_redecide<NC, true>(mu, p, st);
             return cudaGetLastError();
         }
         {   // FP32 plaquette staples (eps = 1): the plaquette-staple link ring
@@ -49,6 +62,7 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
                 default: k_subsweep_pring<NC, 3><<<rb, VS_RING_THREADS, sm, st>>>(p); break;
             }
             count_launches(1);
+            if (p.defer_idx) launch_redecide<NC, false>(mu, p, st);
             return cudaGetLastError();
         }
     }
@@ -72,6 +86,12 @@ cudaError_t launch_subsweep_tpl(bool rect, int mu, const SubsweepParams &p, cuda
     }
 #undef VS_LAUNCH
     count_launches(1);
+    if constexpr (sizeof(T) == 4) {
+        if (p.defer_idx) {
+            if (rect) launch_redecide<NC, true>(mu, p, st);
+            else launch_redecide<NC, false>(mu, p, st);
+        }
+    }
     return cudaGetLastError();
 }
 

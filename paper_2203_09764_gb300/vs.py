@@ -44,7 +44,8 @@ class vs_options(ctypes.Structure):
 
 class vs_anneal(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("rho_per_sweep", ctypes.POINTER(ctypes.c_double)),
-                ("reunit_every", ctypes.c_int32), ("action_every", ctypes.c_int32)]
+                ("reunit_every", ctypes.c_int32), ("action_every", ctypes.c_int32),
+                ("fp64_redecide", ctypes.c_int32)]
 
 
 class vs_sweep_stats(ctypes.Structure):
@@ -52,7 +53,7 @@ class vs_sweep_stats(ctypes.Structure):
                 ("n_fp64_exp", ctypes.c_int64), ("action", ctypes.c_double),
                 ("has_action", ctypes.c_int32), ("n_singular", ctypes.c_int32),
                 ("n_label_diff", ctypes.c_int64), ("n_undecidable", ctypes.c_int64),
-                ("min_margin", ctypes.c_double)]
+                ("min_margin", ctypes.c_double), ("n_fp64_redecided", ctypes.c_int64)]
 
 
 class vs_vortex_report(ctypes.Structure):
@@ -339,9 +340,10 @@ def vs_centrifuge(f, omega, seed):
 
 
 def vs_smooth(f, n_sweeps, rho, epsilon=1.0, u0=1.0, kind=VS_ANNEALED, rho_per_sweep=None,
-              reunit_every=10, action_every=0, vortex_preserve=True, stats=False):
+              reunit_every=10, action_every=0, vortex_preserve=True, stats=False, fp64_redecide=False):
     a = vs_anneal()
     a.kind = kind
+    a.fp64_redecide = 1 if fp64_redecide else 0
     keep = None
     if rho_per_sweep is not None:
         keep = np.ascontiguousarray(rho_per_sweep, dtype=np.float64)
@@ -357,7 +359,7 @@ def vs_smooth(f, n_sweeps, rho, epsilon=1.0, u0=1.0, kind=VS_ANNEALED, rho_per_s
         return None
     return [dict(n_accept=s.n_accept, n_reject=s.n_reject, n_fp64_exp=s.n_fp64_exp,
                  action=(s.action if s.has_action else None), n_label_diff=s.n_label_diff,
-                 n_undecidable=s.n_undecidable, min_margin=s.min_margin)
+                 n_undecidable=s.n_undecidable, min_margin=s.min_margin, n_fp64_redecided=s.n_fp64_redecided)
             for s in st[:int(n_sweeps)]]
 
 

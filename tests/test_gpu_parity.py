@@ -376,6 +376,45 @@ def test_fp32_simultaneous_vp_each_sweep(ctx, eps, rho):
     assert worst < 1e-6
 
 
+@pytest.mark.parametrize("storage", ["link18", "link12"])
+def test_fp32_vp_candidates_near_an_edge_are_redecided_in_fp64(ctx, storage):
+    """Sec. VI test in FP32 with vortex preservation: a candidate whose FP32
+    trace lies within the FP32 band of a sector edge is decided again in FP64
+    from the same stored links (vs_anneal.fp64_redecide).  Along the 200-sweep
+    trajectory, each sweep from the oracle's FP64 field: with the FP64 pass the
+    decisions equal the oracle's except for candidates within the band of the
+    FP32 link storage (n_undecidable), every re-decided candidate is counted,
+    and fewer candidates stay undecidable than with FP32 decisions alone."""
+    dims = (8, 8, 8, 8)
+    lab = cooled_labels(dims, 2)
+    st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, st)
+    tot = {True: dict(split=0, undec=0, redec=0), False: dict(split=0, undec=0, redec=0)}
+    U = O.centrifuge(dims, lab, 0.02, 1234)
+    for sweep in range(200):
+        Unext, rej, cmargin, _ = O.smooth(dims, U, lab, 1, 0.06, eps=-0.25, vp=True, diagnostics=True)
+        for redecide in (True, False):
+            vs.vs_load_field(f, links=U)
+            s1 = vs.vs_smooth(f, 1, 0.06, -0.25, vortex_preserve=True, reunit_every=0, stats=True,
+                              fp64_redecide=redecide)[0]
+            Ug = vs.vs_read_field(f)
+            split = np.abs(Ug - Unext).max(axis=(2, 3)) > 1e-4
+            assert int(split.sum()) <= s1["n_undecidable"], (redecide, sweep, cmargin[split], s1)
+            t = tot[redecide]
+            t["split"] += int(split.sum())
+            t["undec"] += s1["n_undecidable"]
+            t["redec"] += s1["n_fp64_redecided"]
+            if s1["n_undecidable"] == 0:
+                assert s1["n_reject"] == int(rej[0]) and s1["n_label_diff"] == int(rej[0])
+        U = Unext
+    vs.vs_field_destroy(f)
+    print("%s: with FP64 re-decision %s, FP32 alone %s" % (storage, tot[True], tot[False]))
+    assert tot[False]["redec"] == 0
+    assert tot[False]["undec"] > 0 and tot[True]["redec"] > 0
+    assert tot[True]["undec"] <= tot[False]["undec"]
+    assert tot[True]["split"] <= tot[False]["split"]
+
+
 @pytest.mark.parametrize("storage,vp", [("link18", True), ("link12", True), ("link18", False)])
 def test_fp32_each_sweep_within_fp32_rounding_of_fp64(ctx, storage, vp):
     """FP32 accuracy along the whole 200-sweep FP64 trajectory.  The annealed
