@@ -172,3 +172,43 @@ def test_oracle_and_product_share_no_code():
         for m in imp.findall(text(p)):
             assert not (m.startswith("oracle") or m.startswith("paper_2203_09764_gb300")), (p, m)
     assert product_c and glob.glob(os.path.join(ROOT, "oracle", "*.c"))
+
+
+STRUCTS = ["vs_options", "vs_anneal", "vs_sweep_stats", "vs_vortex_report", "vs_observables_out",
+           "vs_field_desc", "vs_job", "vs_result", "vs_serve_stats"]
+
+
+def test_binding_structs_match_the_header(libvs, tmp_path):
+    """Every public struct of include/vs.h and its ctypes mirror in the binding
+    agree on size, field names, order and offsets (compiled with the host C
+    compiler against the header itself)."""
+    import shutil
+    import subprocess
+    from paper_2203_09764_gb300 import vs
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vs.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(vs, name)
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, value = line.split()
+            got[(name, field)] = int(value)
+    for name in STRUCTS:
+        cls = getattr(vs, name)
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
