@@ -956,3 +956,30 @@ def test_aus_and_ucp_per_sweep_label_diffs_fp64(ctx, method, vp):
         assert st[k]["n_undecidable"] == 0 and 0 < st[k]["min_margin"] < np.pi / 3 + 1e-12
         seen += want
     assert seen > 0
+
+
+@pytest.mark.parametrize("kind,storage", [("annealed", "link18"), ("simultaneous", "link18"),
+                                          ("annealed", "link12")])
+def test_fp64_redecision_in_a_random_gauge_keeps_every_label(ctx, kind, storage):
+    """The FP64 re-decision reads the field's gauge transformation G for the
+    gauge-reversed test (Sec. V.D, Sec. VI) and, in the simultaneous schedule,
+    writes the alternate buffer: 60 free-running FP32 sweeps with vortex
+    preservation re-decide candidates, and every gauge-reversed label and
+    centre charge is the original one afterwards."""
+    dims = (16, 16, 16, 32)
+    lab = cooled_labels(dims, 2)
+    G = synth.random_gauge(dims, 43)
+    st = vs.VS_LINK18 if storage == "link18" else vs.VS_LINK12
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, st)
+    vs.vs_load_field(f, labels=lab)
+    vs.vs_centrifuge(f, 0.02, 1234)
+    vs.vs_gauge_transform(f, G)
+    k = vs.VS_ANNEALED if kind == "annealed" else vs.VS_SIMULTANEOUS
+    stats = vs.vs_smooth(f, 60, 0.06, -0.25, kind=k, vortex_preserve=True, stats=True, fp64_redecide=True)
+    chk = vs.vs_vortex_check(f)
+    vs.vs_field_destroy(f)
+    n_redec = sum(s["n_fp64_redecided"] for s in stats)
+    print("%s %s: %d re-decided, %d undecidable, %d rejected" % (
+        kind, storage, n_redec, sum(s["n_undecidable"] for s in stats), sum(s["n_reject"] for s in stats)))
+    assert n_redec > 0
+    assert chk["n_label_diff"] == 0 and chk["n_charge_diff"] == 0
