@@ -439,7 +439,7 @@ __device__ __forceinline__ void count_update(unsigned long long *c, const Update
 
 // Band of a candidate computed in FP64 from FP32-stored links: rounding the
 // links to FP32 moves each entry by up to 6e-8 relative, the candidate's
-// trace by a few 1e-7 (the staple sum adds 48 paths); within this band of an
+// trace by a few 1e-7 (the staple sum adds 24 paths); within this band of an
 // edge the FP32 field itself, not the arithmetic, can decide the test.
 constexpr double kRedecideBand = 1e-6;
 
