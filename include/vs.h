@@ -439,6 +439,7 @@ typedef struct {
     int32_t n_sweeps;
     int32_t reunit_every;
     double *links_out;             /* optional host [4][V][3][3][2], written before completion */
+    int32_t fp64_redecide;         /* as vs_anneal.fp64_redecide (0: FP32 decisions) */
 } vs_job;
 
 typedef struct {

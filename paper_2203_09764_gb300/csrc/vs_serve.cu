@@ -34,7 +34,7 @@ enum JobState { WAITING, RUNNING, DONE };
 // What fixes the node structure of a job's chunk graph.
 struct GraphKey {
     int32_t dims[4];
-    int32_t precision, storage, rect, chunk, reunit_every;
+    int32_t precision, storage, rect, chunk, reunit_every, redecide;
     bool operator<(const GraphKey &o) const {
         return std::memcmp(this, &o, sizeof *this) < 0;
     }
@@ -212,6 +212,7 @@ static vs_status enqueue_chunk(Serve &sv, std::unique_lock<std::mutex> &lk, Job 
     memset(&a, 0, sizeof a);
     a.kind = VS_ANNEALED;
     a.reunit_every = s.reunit_every;
+    a.fp64_redecide = s.fp64_redecide != 0;
     if (n == j.chunk && (s.reunit_every <= 0 || j.chunk % s.reunit_every == 0)) {
         if (!j.graph) {
             cudaGraph_t g = nullptr;
@@ -226,7 +227,7 @@ static vs_status enqueue_chunk(Serve &sv, std::unique_lock<std::mutex> &lk, Job 
             }
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
             j.key = GraphKey{{s.dims[0], s.dims[1], s.dims[2], s.dims[3]}, s.precision, s.storage,
-                             s.epsilon != 1.0, j.chunk, s.reunit_every};
+                             s.epsilon != 1.0, j.chunk, s.reunit_every, s.fp64_redecide != 0};
             lk.lock();
             cudaGraphExec_t pooled = sv.take_graph(j.key);
             lk.unlock();

@@ -83,7 +83,7 @@ class vs_job(ctypes.Structure):
                 ("centrifuge_seed", ctypes.c_uint64), ("rho", ctypes.c_double),
                 ("epsilon", ctypes.c_double), ("u0", ctypes.c_double),
                 ("n_sweeps", ctypes.c_int32), ("reunit_every", ctypes.c_int32),
-                ("links_out", ctypes.c_void_p)]
+                ("links_out", ctypes.c_void_p), ("fp64_redecide", ctypes.c_int32)]
 
 
 class vs_result(ctypes.Structure):
@@ -595,7 +595,7 @@ def vs_debug_expm(ctx, X, precision=VS_FP64):
 
 def make_job(dims, rho, n_sweeps, epsilon=-0.25, u0=1.0, labels=None, seed=0, n_cool=20,
              omega=0.02, centrifuge_seed=1234, vortex_preserve=True, precision=VS_FP32,
-             storage=VS_LINK18, reunit_every=10, links_out=None):
+             storage=VS_LINK18, reunit_every=10, links_out=None, fp64_redecide=False):
     """Build a vs_job; the returned object keeps the label / output arrays alive."""
     j = vs_job()
     for k in range(4):
@@ -617,6 +617,7 @@ def make_job(dims, rho, n_sweeps, epsilon=-0.25, u0=1.0, labels=None, seed=0, n_
     j.u0 = float(u0)
     j.n_sweeps = int(n_sweeps)
     j.reunit_every = int(reunit_every)
+    j.fp64_redecide = 1 if fp64_redecide else 0
     if links_out is not None:
         keep.append(links_out)
         j.links_out = links_out.ctypes.data

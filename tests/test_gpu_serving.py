@@ -244,3 +244,39 @@ def test_chunk_graphs_are_reused_per_shape():
         assert np.array_equal(U, out), (rho, n, seed)
     vs.vs_destroy(ctx)
     assert st["graphs_instantiated"] == 1 and st["graphs_reused"] == 2, st
+
+
+def test_served_job_with_fp64_redecision_equals_direct_pipeline():
+    """A served FP32 job with the FP64 re-decision (vs_job.fp64_redecide: its
+    chunk graphs hold the re-decision launches and are pooled apart from the
+    FP32-decision graphs) gives the links of the same pipeline on a field,
+    alone and in a mix with FP32-decision jobs of the same shape."""
+    from tests.gpu_common import cooled_labels
+    dims = (16, 16, 16, 32)
+    lab = cooled_labels(dims, 2)
+    V = int(np.prod(dims))
+    ctx = vs.vs_create(0)
+    f = vs.vs_field_create(ctx, dims, vs.VS_FP32, vs.VS_LINK18)
+    vs.vs_load_field(f, labels=lab)
+    vs.vs_centrifuge(f, 0.02, 1234)
+    st = vs.vs_smooth(f, 60, 0.06, -0.25, reunit_every=10, stats=True, fp64_redecide=True)
+    U = vs.vs_read_field(f)
+    vs.vs_field_destroy(f)
+    assert sum(s["n_fp64_redecided"] for s in st) > 0
+    outs = []
+    for mix in (False, True):
+        jobs = []
+        if mix:
+            for k in range(2):
+                o = np.empty((4, V, 3, 3), dtype=np.complex128)
+                jobs.append((vs.make_job(dims, 0.05, 40, labels=lab, omega=0.02, centrifuge_seed=1234,
+                                         links_out=o), o))
+        out = np.empty((4, V, 3, 3), dtype=np.complex128)
+        j = vs.make_job(dims, 0.06, 60, labels=lab, omega=0.02, centrifuge_seed=1234, links_out=out,
+                        fp64_redecide=True)
+        tickets = [vs.vs_submit(ctx, jj) for jj, _ in jobs] + [vs.vs_submit(ctx, j)]
+        res = [vs.vs_poll(ctx, t, -1) for t in tickets]
+        assert all(r["status"] == vs.VS_OK for r in res)
+        outs.append(out)
+    vs.vs_destroy(ctx)
+    assert np.array_equal(outs[0], U) and np.array_equal(outs[1], U)
