@@ -109,10 +109,13 @@ __device__ __forceinline__ Pt site_of_lex(const Geo &g, int s) {
 //           b = (c - (x_mu + y + z + t)) mod 4 over the row's (y,z,t) coordinates.
 //  mu == 0: 2x = c - (y+z+t) mod 4 needs c - (y+z+t) even: half the rows hold
 //           Lx/2 class sites, x mod 4 in {b0, b0 + 2}.
+// Odd colours take the sites in reverse order, so that each class launch of a
+// sweep starts where the previous one ended and finds those links still in L2.
 template <int MU>
 __device__ __forceinline__ Pt class_site(const Geo &g, int c, int t) {
     Pt p;
     const int Q = g.Q;
+    if (c & 1) t = g.V / 4 - 1 - t;
     if (MU != 0) {
         int a = t % Q;
         int row = t / Q;
