@@ -40,7 +40,7 @@ BYTES_PER_UPDATE = {(1, 18): 17 * 72 + 1, (1, 12): 17 * 48 + 1, (0, 18): 17 * 14
 FLOPS_PER_UPDATE_OVERIMPROVED = 65 * 216 + 600
 # DRAM bytes (read + write) of one class-update launch of this kernel version,
 # from `ncu --set full` on the same command (profiles/k_subsweep_f32_*.md)
-NCU_TRAFFIC_PER_LAUNCH = 622.623488e6 + 38.182656e6
+NCU_TRAFFIC_PER_LAUNCH = 625.287936e6 + 40.275968e6
 # FP32 FMA peak of the GPU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
