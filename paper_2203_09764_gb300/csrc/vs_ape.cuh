@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     Update<T> up;
     if (active) {
         const Geo &g = a.g;
-        const Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        const Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : dir_site<MU>(g, t);
         const int i = sidx(g, x);
         const T *Us = static_cast<const T *>(a.Usrc);
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_ape_ring(ApeP
     Update<float> up;
     if (active) {
         const Geo &g = a.g;
-        const Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        const Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : dir_site<MU>(g, t);
         const int i = sidx(g, x);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     bool used64 = false;
     if (t < a.n_threads) {
         const Geo &g = a.g;
-        const Pt x = site_of_index(g, t);
+        const Pt x = dir_site<MU>(g, t);
         const int i = sidx(g, x);
         const T *Us = static_cast<const T *>(a.Usrc);
         const bool f32 = sizeof(T) == 4;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, RECT ? VS_RING_MINB : 4) k_fl
     bool used64 = false;
     if (t < a.n_threads) {
         const Geo &g = a.g;
-        const Pt x = site_of_index(g, t);
+        const Pt x = dir_site<MU>(g, t);
         const int i = sidx(g, x);
         const float *Us = static_cast<const float *>(a.Usrc);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);

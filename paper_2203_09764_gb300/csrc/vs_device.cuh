@@ -81,6 +81,14 @@ __device__ __forceinline__ Pt site_of_index(const Geo &g, int i) {
     return p;
 }
 
+// Thread t of a launch over every site of direction MU (the simultaneous
+// schedules and the Runge-Kutta stages): odd directions take the sites in
+// reverse order, so each launch starts where the previous one ended.
+template <int MU>
+__device__ __forceinline__ Pt dir_site(const Geo &g, int t) {
+    return site_of_index(g, (MU & 1) ? g.V - 1 - t : t);
+}
+
 // The site at layout position i (the inverse of sidx on used positions).
 __device__ __forceinline__ Pt site_of_pos(const Geo &g, int i) {
     Pt p;

@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(VS_SUBSWEEP_THREADS, sizeof(T) == 4 ? VS_SUBSW
     Update<T> u;
     if (active) {
         const Geo &g = a.g;
-        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : dir_site<MU>(g, t);
         const int i = sidx(g, x);
         const T *Us = static_cast<const T *>(a.Usrc);
         const T c0 = sizeof(T) == 4 ? T(a.c0_f) : T(a.c0), c1 = sizeof(T) == 4 ? T(a.c1_f) : T(a.c1);
@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, 4) k_subsweep_pring(SubsweepP
     Update<float> u;
     if (active) {
         const Geo &g = a.g;
-        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : dir_site<MU>(g, t);
         const int i = sidx(g, x);
         const float *Us = static_cast<const float *>(a.Usrc);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
@@ -926,7 +926,7 @@ __global__ void __launch_bounds__(VS_RING_THREADS, VS_RING_MINB) k_subsweep_fuse
     Update<float> u;
     if (active) {
         const Geo &g = a.g;
-        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : site_of_index(g, t);
+        Pt x = a.colour >= 0 ? class_site<MU>(g, a.colour, t) : dir_site<MU>(g, t);
         const int i = sidx(g, x);
         LinkRing<NC> R = ring_of<NC>(ring4, ring2);
         M3<float> Ux;
